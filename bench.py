@@ -1,0 +1,304 @@
+"""Throughput benchmark: |M|^2 points/s of e- gamma -> e- + k gamma on B300.
+
+Default workload: e- gamma -> e- + 4 gamma (120 diagrams), 1,048,576 seeded
+RAMBO points at omega = 4 m_e, all 128 helicity/polarisation states summed.
+One step = one evaluation of the whole batch.  The FP32-mixed path gives the
+line's value; the plain FP64 path is timed the same way and reported beside
+it, each with its roofline against the FMA-pipe peak.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own batch (weak scaling) and rank 0
+prints one JSON line.  --impl reference times the CPU oracle on the host
+cores instead (a bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_19456_b300 import phasespace as ps  # noqa: E402
+
+SM_COUNT = 148
+SM_MAX_MHZ = 2032.0
+FP32_LANES_PER_SM = 128
+# Peaks of the FMA pipes from unit counts and the maximum SM clock:
+# FP32 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz; FP64 the nominal B300 rate.
+PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during a timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(mom: np.ndarray, k: int, target_cpu_s: float = 15.0):
+    """The oracle on the host cores, on a bounded sample of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probe = mom[:cores]
+    t0 = time.perf_counter()
+    oracle.m2(probe, threads=cores)
+    per_pt_cpu = (time.perf_counter() - t0) * cores / len(probe)
+    n = int(min(len(mom), max(cores, target_cpu_s / max(per_pt_cpu, 1e-9))))
+    n = max(cores, (n // cores) * cores)
+    sample = mom[cores:cores + n]
+    t0 = time.perf_counter()
+    oracle.m2(sample, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": len(sample) / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(mom)} k={k} points (all states summed), "
+                      f"{dt:.1f} s wall on {cores} threads"}
+
+
+def run_reference(args, workload):
+    """--impl reference: the FP64 oracle on the host cores, one bounded sample per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = ps.WORKLOADS[workload]
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 4 * cores)
+    mom = ps.points(w["k"], per_step * (args.steps + args.warmup), w["omega"], w["seed"])
+    steps = []
+    for s in range(args.warmup + args.steps):
+        chunk = mom[s * per_step:(s + 1) * per_step]
+        t0 = time.perf_counter()
+        oracle.m2(chunk, threads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            steps.append(dt)
+    t = sum(steps)
+    value = per_step * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "k": w["k"], "n_points": per_step,
+                   "states_summed": 2 ** (w["k"] + 3), "omega": w["omega"],
+                   "note": "each step a bounded sample of the workload on the host cores"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} points per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "|M|^2 points/s on 1 B300 (e gamma -> e + k gamma), FP32-mixed vs FP64, % of FLOP peak"
+
+
+def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        plan.eval(d_mom, out, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.eval(d_mom, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / steps  # ms per step
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 path (default: --steps)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args, args.workload)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    barrier = (lambda: dist.barrier()) if ws > 1 else (lambda: None)
+
+    from paper_2511_19456_b300 import Plan, measure_fma_peak
+
+    w = ps.WORKLOADS[args.workload]
+    k, n = w["k"], w["n_points"]
+    mom = ps.points(k, n, w["omega"], w["seed"] + 7919 * rank)
+    d_mom = torch.from_numpy(mom).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    hel = None if w["summed"] else w["hel"]
+
+    res = {}
+    launches = 0
+    clocks = None
+    fp64_steps = args.fp64_steps if args.fp64_steps is not None else args.steps
+    for prec, steps in (("mixed", args.steps), ("fp64", fp64_steps)):
+        plan = Plan(k, summed=w["summed"], hel=hel, precision=prec)
+        info = plan.info()
+        with ClockSampler(local) as cs:
+            ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier)
+        launches += steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        pts = n * ws / (ms * 1e-3)
+        flops = info["flops_per_point"]
+        achieved = flops * n / (ms * 1e-3) / 1e12
+        peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        res[prec] = {"value": pts, "ms_per_step": ms, "plan": plan, "info": info,
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                                  "pipe": "FP32 FMA" if prec == "mixed" else "FP64 FMA",
+                                  "flops_per_point": flops},
+                     "clocks": cs.summary()}
+        if prec == "mixed":
+            clocks = cs.summary()
+
+    # measured FMA-chain peaks (context for the derived peaks above)
+    measured = {"fp32_tflops": measure_fma_peak("mixed"), "fp64_tflops": measure_fma_peak("fp64")}
+
+    # end to end through the public API on pinned host buffers
+    plan = res["mixed"]["plan"]
+    h_mom = torch.from_numpy(mom).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        plan.eval_host(h_mom, h_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_host(h_mom, h_out)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    chunk = min(n, max(1 << 16, (n + 7) // 8))
+    launches += args.steps * math.ceil(n / chunk)
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    mixed, fp64 = res["mixed"], res["fp64"]
+    line = {
+        "metric": METRIC,
+        "value": mixed["value"],
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": mixed["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "k": k, "n_points": n, "omega": w["omega"],
+                   "states_summed": mixed["info"]["n_states"], "diagrams": mixed["info"]["n_diagrams"],
+                   "generator": "RAMBO (seeded SplitMix64)" if k > 1 else "flat 2-body",
+                   "l2": f"inputs {n * (k + 3) * 32 / 1e6:.0f} MB per step, larger than the 126 MB L2",
+                   "precision": "mixed: FP32 currents and Kahan diagram sums; FP64 momenta, "
+                                "denominators, spin sum"},
+        "roofline": mixed["roofline"],
+        "fp64": {"value": fp64["value"], "unit": "points/s", "ms_per_step": fp64["ms_per_step"],
+                 "steps": fp64_steps, "roofline": fp64["roofline"], "clocks": fp64["clocks"]},
+        "speedup_mixed_vs_fp64": mixed["value"] / fp64["value"],
+        "peaks_measured_fma_chain": measured,
+        "e2e": {"value": n * ws / e2e_s, "unit": "points/s",
+                "h2d_bytes_per_step": int(h_mom.numel() * 8),
+                "d2h_bytes_per_step": int(h_out.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mom, k)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * qed.h - C-ABI of the B300 multi-photon Compton |M|^2 engine.
+ *
+ * Process: e-(p) gamma(k0) -> e-(p') + gamma(k1) ... gamma(kK), tree level,
+ * K = k outgoing photons, n = k + 1 photons on the electron line and (k+1)!
+ * Feynman diagrams (paper Sec. III-A).  The amplitude of one diagram follows
+ * the QED Feynman rules of paper Sec. I-B (Eq. 1 is the k = 1 case):
+ *
+ *   A_sigma = ubar(p') eps/_{sigma(n)} S(Q_{n-1}) ... S(Q_1) eps/_{sigma(1)} u(p),
+ *   S(Q) = (Q/ + m) / (Q^2 - m^2),  Q_i = p + sum_{l<=i} c_l k_{sigma(l)},
+ *
+ * with c = +1 for the incoming and -1 for outgoing photons; the constant
+ * factor (-ie)^n i^(n-1) (unit modulus for e = 1) is dropped, and
+ * |M|^2 = sum over the requested spin/polarisation states of |sum_sigma A|^2.
+ * The evaluation goes through the node-reduced computable DAG of paper
+ * Sec. II (node reduction: App. C), built and linearised on the host by
+ * qed_plan_create.
+ *
+ * Conventions (units m = e = 1 by default): metric (+,-,-,-), Dirac
+ * representation, helicity spinors, real linear photon polarisations with
+ * eps^0 = 0 in the frame of the given momenta (polarisation 1 = the state
+ * eps_1 = (kx kz, ky kz, -kT^2)/(|k| kT), polarisation 2 = (-ky, kx, 0)/kT).
+ *
+ * Momentum layout: momenta[N][k+3][4] float64, row-major, slot 0 = e- in,
+ * 1 = gamma in, 2 = e- out, 3..k+2 = gamma out; components (E, px, py, pz).
+ * Propagator momenta are formed from p and the photon momenta of the photons
+ * to the left of the line (p' never enters a propagator).
+ *
+ * Ownership and errors: the caller owns every buffer it passes; a plan owns
+ * its device tables, allocated in qed_plan_create and freed by
+ * qed_plan_destroy.  Every function returns a qed_status and never throws;
+ * arguments are validated before any launch; N = 0 returns QED_OK without a
+ * launch.  Non-finite momenta give non-finite outputs and are not errors.
+ * qed_eval and qed_eval_grad allocate nothing and do not synchronise the
+ * host; a plan is immutable after creation and may be used from several
+ * streams at once.
+ */
+#ifndef QED_H
+#define QED_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qed_plan_s* qed_plan_t;
+typedef struct qed_batch_s* qed_batch_t;
+
+typedef enum {
+  QED_OK = 0,
+  QED_EINVAL = 1,          /* invalid argument (NULL, range, misaligned)   */
+  QED_ENOMEM = 2,          /* host or device allocation failed             */
+  QED_ECUDA = 3,           /* a CUDA runtime call failed                   */
+  QED_EUNSUPPORTED = 4,    /* valid request this build does not provide    */
+  QED_EDEVICE_TIMEOUT = 5  /* a bounded device-side wait ran out           */
+} qed_status;
+
+typedef enum {
+  QED_FP64 = 0,   /* every step in FP64                                    */
+  QED_MIXED = 1   /* spinors, currents and diagram sums in FP32 with a
+                     compensated (Kahan) diagram sum; momenta, propagator
+                     denominators and the spin sum in FP64                 */
+} qed_precision;
+
+/* Process e- gamma -> e- + k gamma, k in [1, 7].  mass: electron mass
+ * (> 0); charge: the coupling e, |M|^2 is multiplied by e^(2(k+1)). */
+typedef struct {
+  int k;
+  double mass;
+  double charge;
+} qed_process;
+
+/* Spin / polarisation selection.  summed != 0: all 2^(k+3) states summed.
+ * Otherwise one fixed state: hel[slot] for slot 0..k+2 with electrons
+ * (slots 0, 2) in {+1, -1} (helicity) and photons in {1, 2}
+ * (polarisation). */
+typedef struct {
+  int summed;
+  signed char hel[10];
+} qed_spin_cfg;
+
+/* Sizes of a plan's DAG and its counted arithmetic. */
+typedef struct {
+  int k;
+  int n_photons;               /* k + 1                                    */
+  long long n_diagrams;        /* (k+1)!                                   */
+  long long n_states;          /* spin/polarisation states summed (or 1)   */
+  long long nodes_unreduced;   /* per-diagram CDAG, data + compute nodes,
+                                  one spin state (paper Table I)           */
+  long long nodes_reduced;     /* after node reduction to the fixpoint     */
+  long long compute_reduced;   /* compute nodes of the reduced DAG         */
+  long long v_nodes, s1_nodes, s2_nodes; /* reduced, times spin variants  */
+  long long flops_per_point;   /* algorithmic FLOPs of the reduced DAG
+                                  (add/sub/mul 1, fma 2, div/sqrt 1)       */
+  long long flops_executed_per_point; /* including recomputed currents     */
+  long long flops_literal_s2_per_point; /* if every S2 propagated itself  */
+  int team_threads;            /* threads cooperating on one point         */
+  int smem_bytes_per_team;
+  int precision;               /* qed_precision                            */
+} qed_plan_info_t;
+
+/* Counts of the CDAG of one spin state, computed on the host without a GPU
+ * (paper Table I and Fig. graph_size).  For k <= 7 the DAG is built node by
+ * node and node-reduced to its fixpoint (paper App. C); for k = 8 only the
+ * unreduced counts are given (from the same per-diagram construction, in
+ * closed form) and the reduced fields are -1. */
+typedef struct {
+  long long unreduced_total, unreduced_data, unreduced_u, unreduced_v,
+            unreduced_s1, unreduced_s2, unreduced_sum;
+  long long reduced_total, reduced_data, reduced_u, reduced_v,
+            reduced_s1, reduced_s2, reduced_sum;
+} qed_dag_counts_t;
+
+/* Build the CDAG for a process on the host (paper Sec. II-A: generator,
+ * optimiser by node reduction, linear schedule), upload its tables and
+ * pick the kernel for `precision`.  Requires a CUDA device for the upload.
+ * Errors: QED_EINVAL for NULL pointers, k outside [1, 7], mass <= 0 or a bad
+ * fixed state; QED_ENOMEM; QED_ECUDA.  *out is set only on QED_OK. */
+qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
+                           qed_precision precision, qed_plan_t* out);
+
+qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
+
+/* out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4
+ * doubles, 8-byte aligned; d_out_m2: device pointer to N doubles; stream: a
+ * cudaStream_t (NULL = legacy default stream).  Asynchronous. */
+qed_status qed_eval(qed_plan_t plan, const double* d_momenta, long long n,
+                    double* d_out_m2, void* stream);
+
+/* As qed_eval, plus d_grad[N][k][3] = d|M|^2 / d(px, py, pz) of the k
+ * outgoing photons (slots 3..k+2), their energies on shell, E_j = |k_j|, and
+ * every other momentum held fixed.  d_out_m2 may be NULL. */
+qed_status qed_eval_grad(qed_plan_t plan, const double* d_momenta, long long n,
+                         double* d_out_m2, double* d_grad, void* stream);
+
+/* End-to-end form of qed_eval on HOST buffers: copies the momenta to the
+ * device, evaluates and copies |M|^2 back, chunked so that copies overlap
+ * the kernels.  Uses device staging owned by the plan, grown (allocated) on
+ * the first call that needs more; synchronises `stream` before returning.
+ * Host buffers should be page-locked for full copy bandwidth. */
+qed_status qed_eval_host(qed_plan_t plan, const double* h_momenta, long long n,
+                         double* h_out_m2, void* stream);
+
+void qed_plan_destroy(qed_plan_t plan);
+
+qed_status qed_dag_counts(int k, qed_dag_counts_t* out);
+
+const char* qed_status_string(qed_status status);
+
+/* Measured FMA-pipe peak of the current device in TFLOP/s: FP64 for
+ * QED_FP64, FP32 for QED_MIXED (independent FMA chains on every SM, CUDA
+ * events on `stream`; allocates a small scratch buffer; synchronises).  The
+ * |M|^2 kernels are bound by this pipe, so it is their roofline
+ * denominator. */
+qed_status qed_measure_fma_peak(qed_precision precision, double* tflops, void* stream);
+
+/* Linear schedule of the node-reduced DAG, as the kernels execute it: V (+S1)
+ * instructions (16 bytes each), phases (24 bytes) and photon-set entries (16
+ * bytes); layouts in csrc/dag.hpp.  Host only, no GPU needed.  Call with NULL
+ * buffers to get the sizes in *desc, then with buffers of those sizes. */
+typedef struct {
+  int k, n, h, r, ls, rs, summed;
+  int n_left_leaves, n_right_leaves, stored_currents, local_currents;
+  int n_stored_phases, n_set_phases, n_sets, n_instr, n_phases;
+  long long flops_algorithmic, flops_executed;
+} qed_schedule_desc_t;
+
+qed_status qed_schedule_export(int k, int summed, qed_schedule_desc_t* desc, void* instr,
+                               void* phases, void* sets);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QED_H */

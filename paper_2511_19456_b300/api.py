@@ -1,0 +1,169 @@
+"""Python front end of the C-ABI: plans, evaluation on device or host buffers.
+
+PyTorch supplies device memory and streams; the arithmetic runs in the
+library's kernels.  Momenta are float64 tensors of shape [N, k+3, 4] (slot 0
+e- in, 1 gamma in, 2 e- out, 3.. gamma out; components E, px, py, pz).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import check
+
+_PREC = {"fp64": _lib.QED_FP64, "mixed": _lib.QED_MIXED}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A built CDAG for e- gamma -> e- + k gamma with its device tables.
+
+    summed=True sums |M|^2 over all 2^(k+3) helicity/polarisation states;
+    otherwise `hel` gives one state per slot (electrons +1/-1, photons 1/2).
+    precision: "fp64" or "mixed".
+    """
+
+    def __init__(self, k: int, summed: bool = True, hel=None, precision: str = "fp64",
+                 mass: float = 1.0, charge: float = 1.0):
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {sorted(_PREC)}")
+        L = _lib.lib()
+        proc = _lib.Process(int(k), float(mass), float(charge))
+        spin = _lib.SpinCfg()
+        spin.summed = 1 if summed else 0
+        if not summed:
+            if hel is None or len(hel) != k + 3:
+                raise ValueError("a fixed state needs hel with k+3 entries")
+            for i, v in enumerate(hel):
+                spin.hel[i] = int(v)
+        handle = ctypes.c_void_p()
+        check(L.qed_plan_create(ctypes.byref(proc), ctypes.byref(spin), _PREC[precision],
+                                ctypes.byref(handle)), "qed_plan_create")
+        self._h = handle
+        self.k = int(k)
+        self.summed = bool(summed)
+        self.hel = None if summed else list(hel)
+        self.precision = precision
+        self.mass = float(mass)
+
+    # -------------------------------------------------------------- info
+    def info(self) -> dict:
+        inf = _lib.PlanInfo()
+        check(_lib.lib().qed_plan_info(self._h, ctypes.byref(inf)), "qed_plan_info")
+        return {f: getattr(inf, f) for f, _ in _lib.PlanInfo._fields_}
+
+    def _check_momenta(self, momenta, device: bool):
+        torch = _torch()
+        if momenta.dtype != torch.float64:
+            raise TypeError("momenta must be float64")
+        if momenta.dim() != 3 or momenta.shape[1] != self.k + 3 or momenta.shape[2] != 4:
+            raise ValueError(f"momenta must have shape [N, {self.k + 3}, 4]")
+        if not momenta.is_contiguous():
+            raise ValueError("momenta must be contiguous")
+        if device and not momenta.is_cuda:
+            raise ValueError("momenta must be a CUDA tensor")
+        if not device and momenta.is_cuda:
+            raise ValueError("momenta must be a host tensor")
+
+    # -------------------------------------------------------------- eval
+    def eval(self, momenta, out=None, stream=None):
+        """|M|^2 per point on the device (asynchronous on `stream`)."""
+        torch = _torch()
+        self._check_momenta(momenta, device=True)
+        n = momenta.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=momenta.device)
+        check(_lib.lib().qed_eval(self._h, ctypes.c_void_p(momenta.data_ptr()), n,
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+              "qed_eval")
+        return out
+
+    def eval_grad(self, momenta, out=None, grad=None, stream=None):
+        """(|M|^2, d|M|^2/d k_j) with k_j the outgoing photons' 3-momenta."""
+        torch = _torch()
+        self._check_momenta(momenta, device=True)
+        n = momenta.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=momenta.device)
+        if grad is None:
+            grad = torch.empty((n, self.k, 3), dtype=torch.float64, device=momenta.device)
+        check(_lib.lib().qed_eval_grad(self._h, ctypes.c_void_p(momenta.data_ptr()), n,
+                                       ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(grad.data_ptr()), _stream_handle(stream)),
+              "qed_eval_grad")
+        return out, grad
+
+    def eval_host(self, momenta, out=None, stream=None):
+        """End to end on host buffers: copy in, evaluate, copy back (synchronous)."""
+        torch = _torch()
+        self._check_momenta(momenta, device=False)
+        n = momenta.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, pin_memory=momenta.is_pinned())
+        check(_lib.lib().qed_eval_host(self._h, ctypes.c_void_p(momenta.data_ptr()), n,
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+              "qed_eval_host")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().qed_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dag_counts(k: int) -> dict:
+    """Node counts of the per-diagram CDAG and of its node-reduced form."""
+    c = _lib.DagCounts()
+    check(_lib.lib().qed_dag_counts(int(k), ctypes.byref(c)), "qed_dag_counts")
+    return {f: getattr(c, f) for f, _ in _lib.DagCounts._fields_}
+
+
+INSTR_DTYPE = np.dtype([("dst", "<i4"), ("src", "<i4"), ("side", "u1"), ("photon", "u1"),
+                        ("rank", "u1"), ("level", "u1"), ("post", "<u2"), ("pad", "<u2")])
+PHASE_DTYPE = np.dtype([("beg", "<i4", 2), ("cnt", "<i4", 2), ("level", "<i4", 2)])
+SET_DTYPE = np.dtype([("mask", "<u4"), ("phase0", "<i4"), ("leaf_l", "<i4"), ("leaf_r", "<i4")])
+
+
+def schedule_export(k: int, summed: bool) -> dict:
+    """The linear schedule the kernels execute, as numpy structured arrays."""
+    L = _lib.lib()
+    d = _lib.ScheduleDesc()
+    check(L.qed_schedule_export(int(k), int(summed), ctypes.byref(d), None, None, None),
+          "qed_schedule_export")
+    instr = np.zeros(d.n_instr, dtype=INSTR_DTYPE)
+    phases = np.zeros(d.n_phases, dtype=PHASE_DTYPE)
+    sets = np.zeros(d.n_sets, dtype=SET_DTYPE)
+    check(L.qed_schedule_export(int(k), int(summed), ctypes.byref(d),
+                                instr.ctypes.data_as(ctypes.c_void_p),
+                                phases.ctypes.data_as(ctypes.c_void_p),
+                                sets.ctypes.data_as(ctypes.c_void_p)), "qed_schedule_export")
+    out = {f: getattr(d, f) for f, _ in _lib.ScheduleDesc._fields_}
+    out.update(instr=instr, phases=phases, sets=sets)
+    return out
+
+
+def measure_fma_peak(precision: str = "fp64", stream=None) -> float:
+    """FMA-pipe peak of the current device in TFLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double()
+    check(_lib.lib().qed_measure_fma_peak(_PREC[precision], ctypes.byref(v), _stream_handle(stream)),
+          "qed_measure_fma_peak")
+    return v.value

@@ -1,0 +1,404 @@
+// Host-side CDAG generator, node reduction and linear schedule.
+// Paper: Sec. II-A (generator, optimiser, scheduler), Sec. II-B (the QED
+// tasks U, V, S1, S2, Sum), Table I (node counts), App. C (node reduction).
+#include "dag.hpp"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+#include <unordered_map>
+
+namespace qed {
+
+int Dag::add(NodeKind k, int f, const int32_t* par, int npar) {
+  if (pbeg.empty()) pbeg.push_back(0);
+  kind.push_back(k);
+  fn.push_back(f);
+  for (int i = 0; i < npar; ++i) parents.push_back(par[i]);
+  pbeg.push_back((int32_t)parents.size());
+  return (int)kind.size() - 1;
+}
+
+Counts Dag::counts() const {
+  Counts c;
+  for (uint8_t k : kind) {
+    ++c.total;
+    switch (k) {
+      case K_DATA: ++c.data; break;
+      case K_U: ++c.u; break;
+      case K_V: ++c.v; break;
+      case K_S1: ++c.s1; break;
+      case K_S2: ++c.s2; break;
+      case K_SUM: ++c.sum; break;
+    }
+  }
+  return c;
+}
+
+namespace {
+
+inline int photon_slot(int j) { return j == 0 ? 1 : j + 2; }
+
+// compute node followed by its output data node; returns the data node
+int emit(Dag& g, NodeKind k, int f, std::initializer_list<int32_t> par) {
+  std::vector<int32_t> p(par);
+  int c = g.add(k, f, p.data(), (int)p.size());
+  int32_t cc = c;
+  return g.add(K_DATA, -1, &cc, 1);
+}
+
+long long factorial(int n) {
+  long long f = 1;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+long long falling(int n, int i) {  // n! / (n-i)!
+  long long f = 1;
+  for (int t = 0; t < i; ++t) f *= (n - t);
+  return f;
+}
+
+}  // namespace
+
+Dag generate(int k) {
+  const int n = k + 1;
+  const int nslots = k + 3;
+  const int h = (n + 1) / 2;
+  Dag g;
+  // entry data nodes (one per external particle, tagged by slot), their U
+  // tasks and U output data nodes
+  std::vector<int32_t> udata(nslots);
+  for (int s = 0; s < nslots; ++s) {
+    int e = g.add(K_DATA, 1000 + s, nullptr, 0);
+    udata[s] = emit(g, K_U, s, {e});
+  }
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<int32_t> diagrams;
+  do {
+    // left half: photons perm[0..h-1] from the incoming electron
+    int32_t cur = udata[0];
+    for (int i = 0; i < h; ++i) {
+      cur = emit(g, K_V, 0, {udata[photon_slot(perm[i])], cur});
+      if (i + 1 < h) cur = emit(g, K_S1, 0, {cur});
+    }
+    int32_t left = cur;
+    // right half: photons perm[n-1], perm[n-2], ... from the outgoing electron
+    cur = udata[2];
+    for (int i = n - 1; i >= h; --i) {
+      cur = emit(g, K_V, 0, {udata[photon_slot(perm[i])], cur});
+      if (i > h) cur = emit(g, K_S1, 0, {cur});
+    }
+    diagrams.push_back(emit(g, K_S2, 0, {left, cur}));
+  } while (std::next_permutation(perm.begin(), perm.end()));
+  int s = g.add(K_SUM, 0, diagrams.data(), (int)diagrams.size());
+  int32_t ss = s;
+  g.add(K_DATA, -1, &ss, 1);
+  return g;
+}
+
+Counts unreduced_counts(int k) {
+  const long long n = k + 1;
+  const long long d = factorial(k + 1);
+  Counts c;
+  c.u = k + 3;
+  c.v = d * n;
+  c.s1 = d * (n - 2);
+  c.s2 = d;
+  c.sum = 1;
+  const long long compute = c.u + c.v + c.s1 + c.s2 + c.sum;
+  c.data = (k + 3) + compute;
+  c.total = c.data + compute;
+  return c;
+}
+
+namespace {
+struct KeyHash {
+  size_t operator()(const std::vector<int64_t>& v) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t x : v) {
+      h ^= (uint64_t)x + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+}  // namespace
+
+Dag reduce(const Dag& in, std::vector<int32_t>* rep_out) {
+  // Single pass in topological order: a node's parents are already mapped to
+  // their representatives, so nodes that agree in function and parent set
+  // map to the same key.  This reaches the fixpoint of repeated reductions.
+  Dag out;
+  std::vector<int32_t> rep(in.size());
+  std::unordered_map<std::vector<int64_t>, int32_t, KeyHash> seen;
+  seen.reserve(in.size());
+  std::vector<int64_t> key;
+  std::vector<int32_t> par;
+  for (int i = 0; i < in.size(); ++i) {
+    par.clear();
+    for (int p = in.pbeg[i]; p < in.pbeg[i + 1]; ++p) par.push_back(rep[in.parents[p]]);
+    std::sort(par.begin(), par.end());
+    par.erase(std::unique(par.begin(), par.end()), par.end());
+    key.assign({(int64_t)in.kind[i], (int64_t)in.fn[i]});
+    for (int32_t p : par) key.push_back(p);
+    auto it = seen.find(key);
+    if (it != seen.end()) {
+      rep[i] = it->second;
+    } else {
+      int id = out.add((NodeKind)in.kind[i], in.fn[i], par.data(), (int)par.size());
+      seen.emplace(key, id);
+      rep[i] = id;
+    }
+  }
+  if (rep_out) *rep_out = std::move(rep);
+  return out;
+}
+
+int nvar(bool summed, int level) { return summed ? (1 << (level + 1)) : 1; }
+
+namespace {
+
+struct VInfo {
+  int side = -1;        // 0 left (from e- in), 1 right (from e- out)
+  int level = 0;
+  int photon = -1;
+  int parent = -1;      // parent V (reduced DAG id) or -1
+  uint32_t set = 0;
+  bool has_s1 = false;
+  bool in_s2 = false;
+};
+
+int rank_in(uint32_t set, int j) { return __builtin_popcount(set & ((1u << j) - 1)); }
+
+}  // namespace
+
+Schedule build_schedule(int k, bool summed, int ls, int rs) {
+  if (k < 1 || k > 7) throw std::runtime_error("k out of range");
+  Schedule sc;
+  sc.k = k;
+  sc.n = k + 1;
+  sc.h = (sc.n + 1) / 2;
+  sc.r = sc.n - sc.h;
+  sc.summed = summed;
+  sc.ls = std::max(0, std::min(ls, sc.h - 1));
+  sc.rs = std::max(0, std::min(rs, sc.r - 1));
+  const int n = sc.n, h = sc.h, r = sc.r;
+  const uint32_t all = (1u << n) - 1;
+
+  Dag g = generate(k);
+  sc.unreduced = g.counts();
+  Dag d = reduce(g);
+  sc.reduced = d.counts();
+
+  // ---- recover the structure of the reduced DAG
+  const int N = d.size();
+  std::vector<int> slot_of_udata(N, -1);   // U output data node -> slot
+  std::vector<int> producer(N, -1);        // data node -> its compute node
+  for (int i = 0; i < N; ++i) {
+    if (d.kind[i] == K_DATA && d.pbeg[i + 1] - d.pbeg[i] == 1) {
+      int c = d.parents[d.pbeg[i]];
+      producer[i] = c;
+      if (d.kind[c] == K_U) slot_of_udata[i] = d.fn[c];
+    }
+  }
+  auto photon_of_slot = [](int s) { return s == 1 ? 0 : (s >= 3 ? s - 2 : -1); };
+  std::vector<VInfo> vi(N);
+  std::vector<std::pair<int, int>> s2list;
+  for (int i = 0; i < N; ++i) {
+    if (d.kind[i] == K_V) {
+      int a = d.parents[d.pbeg[i]], b = d.parents[d.pbeg[i] + 1];
+      int ph = -1, cur = -1;
+      for (int x : {a, b}) {
+        int s = slot_of_udata[x];
+        if (s >= 0 && photon_of_slot(s) >= 0) ph = photon_of_slot(s); else cur = x;
+      }
+      if (ph < 0 || cur < 0 || d.pbeg[i + 1] - d.pbeg[i] != 2)
+        throw std::runtime_error("malformed V node");
+      VInfo& v = vi[i];
+      v.photon = ph;
+      int src = producer[cur];
+      if (d.kind[src] == K_U) {
+        v.side = (d.fn[src] == 0) ? 0 : (d.fn[src] == 2 ? 1 : -1);
+        if (v.side < 0) throw std::runtime_error("V attached to a photon state");
+        v.level = 1;
+        v.set = 1u << ph;
+      } else if (d.kind[src] == K_S1) {
+        int pv = producer[d.parents[d.pbeg[src]]];
+        if (d.kind[pv] != K_V) throw std::runtime_error("S1 not after V");
+        v.side = vi[pv].side;
+        v.level = vi[pv].level + 1;
+        v.parent = pv;
+        v.set = vi[pv].set | (1u << ph);
+      } else {
+        throw std::runtime_error("V input is neither U nor S1");
+      }
+    } else if (d.kind[i] == K_S1) {
+      int pv = producer[d.parents[d.pbeg[i]]];
+      vi[pv].has_s1 = true;
+    } else if (d.kind[i] == K_S2) {
+      int a = producer[d.parents[d.pbeg[i]]], b = producer[d.parents[d.pbeg[i] + 1]];
+      if (vi[a].side == 1) std::swap(a, b);
+      vi[a].in_s2 = vi[b].in_s2 = true;
+      s2list.emplace_back(a, b);
+    }
+  }
+  // ---- check the reduced DAG is the pair of prefix/suffix tries
+  std::vector<std::vector<int>> lv(h + 1), rv(r + 1);
+  for (int i = 0; i < N; ++i) {
+    if (d.kind[i] != K_V) continue;
+    const VInfo& v = vi[i];
+    if (v.side == 0) lv.at(v.level).push_back(i); else rv.at(v.level).push_back(i);
+    bool leaf = (v.side == 0) ? v.level == h : v.level == r;
+    if (leaf != v.in_s2 || leaf == v.has_s1) throw std::runtime_error("unexpected trie shape");
+  }
+  for (int i = 1; i <= h; ++i)
+    if ((long long)lv[i].size() != falling(n, i)) throw std::runtime_error("left level size");
+  for (int i = 1; i <= r; ++i)
+    if ((long long)rv[i].size() != falling(n, i)) throw std::runtime_error("right level size");
+  if ((long long)s2list.size() != factorial(n)) throw std::runtime_error("S2 count");
+  for (auto& pr : s2list)
+    if ((vi[pr.first].set | vi[pr.second].set) != all || (vi[pr.first].set & vi[pr.second].set))
+      throw std::runtime_error("S2 halves do not partition the photons");
+
+  // ---- storage and instructions
+  std::vector<int> index(N, -1);
+  int next = 0;
+  auto make_instr = [&](int node, int dst, int src) {
+    const VInfo& v = vi[node];
+    Instr in{};
+    in.dst = dst;
+    in.src = src;
+    in.side = (uint8_t)v.side;
+    in.photon = (uint8_t)v.photon;
+    in.rank = (uint8_t)rank_in(v.set, v.photon);
+    in.level = (uint8_t)v.level;
+    if (v.side == 0) in.post = v.has_s1 ? (uint16_t)v.set : 0;
+    else in.post = (uint16_t)(all & ~v.set);  // inner: S1; leaf: hoisted S2 propagation
+    return in;
+  };
+  auto push_range = [&](Phase& ph, int slot, int beg, int cnt, int level) {
+    ph.beg[slot] = beg;
+    ph.cnt[slot] = cnt;
+    ph.level[slot] = level;
+  };
+  // stored levels
+  const int nsp = std::max(sc.ls, sc.rs);
+  for (int dlev = 1; dlev <= nsp; ++dlev) {
+    Phase ph{};
+    int slot = 0;
+    for (int side = 0; side < 2; ++side) {
+      int lim = side == 0 ? sc.ls : sc.rs;
+      if (dlev > lim) continue;
+      auto& lst = side == 0 ? lv[dlev] : rv[dlev];
+      int beg = (int)sc.instr.size();
+      for (int node : lst) {
+        index[node] = next;
+        int src = vi[node].parent >= 0 ? index[vi[node].parent] : -1;
+        sc.instr.push_back(make_instr(node, next, src));
+        next += nvar(summed, dlev);
+      }
+      push_range(ph, slot++, beg, (int)lst.size(), dlev);
+    }
+    sc.phases.push_back(ph);
+  }
+  sc.n_stored_phases = (int)sc.phases.size();
+  sc.stored_currents = next;
+
+  // per photon set S (|S| = h): local levels
+  sc.n_set_phases = std::max(h - sc.ls, r - sc.rs);
+  sc.n_left_leaves = (int)factorial(h);
+  sc.n_right_leaves = (int)factorial(r);
+  std::vector<uint32_t> setmasks;
+  for (uint32_t m = 0; m <= all; ++m)
+    if (__builtin_popcount(m) == h) setmasks.push_back(m);
+  int local_size = -1;
+  std::vector<int> lindex(N, -1);
+  for (uint32_t S : setmasks) {
+    SetEntry se{};
+    se.mask = S;
+    se.phase0 = (int)sc.phases.size();
+    int lnext = sc.stored_currents;
+    std::vector<int> touched;
+    // assign local indices: left levels ls+1..h, then right levels rs+1..r
+    std::vector<std::vector<int>> lloc(h + 1), rloc(r + 1);
+    for (int dl = sc.ls + 1; dl <= h; ++dl)
+      for (int node : lv[dl])
+        if ((vi[node].set & ~S) == 0) lloc[dl].push_back(node);
+    for (int dl = sc.rs + 1; dl <= r; ++dl)
+      for (int node : rv[dl])
+        if ((vi[node].set & S) == 0) rloc[dl].push_back(node);
+    if ((int)lloc[h].size() != sc.n_left_leaves || (int)rloc[r].size() != sc.n_right_leaves)
+      throw std::runtime_error("leaf count per set");
+    for (int dl = sc.ls + 1; dl <= h; ++dl) {
+      if (dl == h) se.leaf_l = lnext;
+      for (int node : lloc[dl]) { lindex[node] = lnext; touched.push_back(node); lnext += nvar(summed, dl); }
+    }
+    for (int dl = sc.rs + 1; dl <= r; ++dl) {
+      if (dl == r) se.leaf_r = lnext;
+      for (int node : rloc[dl]) { lindex[node] = lnext; touched.push_back(node); lnext += nvar(summed, dl); }
+    }
+    if (local_size < 0) local_size = lnext - sc.stored_currents;
+    else if (local_size != lnext - sc.stored_currents) throw std::runtime_error("set size");
+    auto src_of = [&](int node) {
+      int p = vi[node].parent;
+      if (p < 0) return -1;
+      return lindex[p] >= 0 ? lindex[p] : index[p];
+    };
+    for (int t = 1; t <= sc.n_set_phases; ++t) {
+      Phase ph{};
+      int slot = 0;
+      for (int side = 0; side < 2; ++side) {
+        int dl = (side == 0 ? sc.ls : sc.rs) + t;
+        int lim = side == 0 ? h : r;
+        if (dl > lim) continue;
+        auto& lst = side == 0 ? lloc[dl] : rloc[dl];
+        int beg = (int)sc.instr.size();
+        for (int node : lst) {
+          int src = src_of(node);
+          if (vi[node].parent >= 0 && src < 0) throw std::runtime_error("missing parent");
+          sc.instr.push_back(make_instr(node, lindex[node], src));
+        }
+        push_range(ph, slot++, beg, (int)lst.size(), dl);
+      }
+      sc.phases.push_back(ph);
+    }
+    for (int node : touched) lindex[node] = -1;
+    sc.sets.push_back(se);
+  }
+  sc.local_currents = local_size;
+
+  // ---- arithmetic counts
+  const long long P = summed ? (1ll << (n + 2)) : 1;
+  long long alg = 0, lit = 0;
+  for (int i = 0; i < N; ++i) {
+    if (d.kind[i] != K_V) continue;
+    const VInfo& v = vi[i];
+    long long nv = nvar(summed, v.level);
+    sc.v_nodes += nv;
+    alg += nv * FLOP_V;
+    bool post = (v.side == 0) ? v.has_s1 : true;
+    bool real_s1 = v.has_s1;
+    if (post) alg += nv * FLOP_S1;
+    if (real_s1) { sc.s1_nodes += nv; lit += nv * FLOP_S1; }
+    lit += nv * FLOP_V;
+  }
+  sc.s2_nodes = factorial(n) * P;
+  long long fixed_cost = ((1ll << n) - 2) * FLOP_SUBSET + 4ll * FLOP_SPINOR + 2ll * n * FLOP_POL +
+                         P * FLOP_SQUARE;
+  alg += sc.s2_nodes * FLOP_JOIN + fixed_cost;
+  lit += sc.s2_nodes * (FLOP_JOIN + FLOP_S1) + fixed_cost;
+  long long exec = fixed_cost + sc.s2_nodes * FLOP_JOIN;
+  for (const Instr& in : sc.instr) {
+    long long nv = nvar(summed, in.level);
+    exec += nv * (FLOP_V + (in.post ? FLOP_S1 : 0));
+  }
+  sc.flops_algorithmic = alg;
+  sc.flops_literal_s2 = lit;
+  sc.flops_executed = exec;
+  return sc;
+}
+
+}  // namespace qed

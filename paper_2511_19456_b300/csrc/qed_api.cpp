@@ -1,0 +1,377 @@
+// C-ABI of the |M|^2 engine (declared in include/qed.h): plan creation (DAG
+// generation, node reduction, linear schedule, upload), evaluation entry
+// points and argument validation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "../../include/qed.h"
+#include "dag.hpp"
+#include "qed_types.h"
+
+namespace qed {
+struct KernelChoice {
+  void (*fn)(const KParams);
+  int team;
+};
+KernelChoice forward_kernel(int k, bool summed, bool mixed);
+cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
+                           cudaStream_t st, const KParams& p);
+}  // namespace qed
+
+using namespace qed;
+
+struct qed_plan_s {
+  int k = 0;
+  bool summed = true;
+  qed_precision prec = QED_FP64;
+  double mass = 1.0, charge = 1.0;
+  Schedule sc;
+  Instr* d_instr = nullptr;
+  Phase* d_phases = nullptr;
+  SetEntry* d_sets = nullptr;
+  KernelChoice kc{nullptr, 0};
+  int block = 0, grid = 0;
+  size_t smem = 0;
+  int team_bytes = 0;
+  int fixed_sin = 0, fixed_sout = 0, fixed_pol[8] = {0};
+  int device = 0;
+  // staging for qed_eval_host
+  double* d_stage = nullptr;
+  long long stage_cap = 0;    // points per buffer
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
+              ev_d2h[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+// Levels kept for the whole point; deeper levels are rebuilt per photon set.
+// All levels below the leaves fit in shared memory except for spin-summed
+// k = 6, 7, where only the first levels are kept.
+void default_levels(int k, bool summed, int* ls, int* rs) {
+  const int n = k + 1, h = (n + 1) / 2, r = n - h;
+  *ls = h - 1;
+  *rs = r - 1;
+  if (summed && k == 6) { *ls = 2; *rs = 2; }
+  if (summed && k == 7) { *ls = 1; *rs = 1; }
+}
+
+qed_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QED_OK;
+  if (e == cudaErrorMemoryAllocation) return QED_ENOMEM;
+  return QED_ECUDA;
+}
+
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+void free_plan(qed_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->d_instr);
+  cudaFree(p->d_phases);
+  cudaFree(p->d_sets);
+  cudaFree(p->d_stage);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
+    if (p->ev_k[i]) cudaEventDestroy(p->ev_k[i]);
+    if (p->ev_d2h[i]) cudaEventDestroy(p->ev_d2h[i]);
+  }
+  if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+  if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+  delete p;
+}
+
+KParams make_params(const qed_plan_s* P, const double* mom, long long n, double* out) {
+  KParams kp{};
+  kp.mom = mom;
+  kp.out = out;
+  kp.n = n;
+  kp.instr = P->d_instr;
+  kp.phases = P->d_phases;
+  kp.sets = P->d_sets;
+  kp.n_stored_phases = P->sc.n_stored_phases;
+  kp.n_set_phases = P->sc.n_set_phases;
+  kp.n_sets = (int)P->sc.sets.size();
+  kp.ncur = P->sc.stored_currents + P->sc.local_currents;
+  kp.team_bytes = P->team_bytes;
+  kp.mass = P->mass;
+  kp.coupling = std::pow(P->charge, 2.0 * (P->k + 1));
+  kp.fixed_sin = P->fixed_sin;
+  kp.fixed_sout = P->fixed_sout;
+  kp.fixed_pol_bits = 0;
+  for (int j = 0; j < 8; ++j) kp.fixed_pol_bits |= (unsigned)(P->fixed_pol[j] & 1) << j;
+  return kp;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+qed_status launch_eval(const qed_plan_s* P, const double* d_mom, long long n, double* d_out,
+                       cudaStream_t st) {
+  if (n == 0) return QED_OK;
+  KParams kp = make_params(P, d_mom, n, d_out);
+  const int tpc = P->block / P->kc.team;
+  long long need = (n + tpc - 1) / tpc;
+  int grid = (int)std::min<long long>(need, P->grid);
+  return cuda_status(launch_forward(P->kc.fn, grid, P->block, P->smem, st, kp));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qed_status_string(qed_status s) {
+  switch (s) {
+    case QED_OK: return "ok";
+    case QED_EINVAL: return "invalid argument";
+    case QED_ENOMEM: return "out of memory";
+    case QED_ECUDA: return "CUDA runtime error";
+    case QED_EUNSUPPORTED: return "unsupported request";
+    case QED_EDEVICE_TIMEOUT: return "device-side wait timed out";
+  }
+  return "unknown status";
+}
+
+qed_status qed_dag_counts(int k, qed_dag_counts_t* out) {
+  if (!out || k < 1 || k > 8) return QED_EINVAL;
+  try {
+    Counts u = unreduced_counts(k);
+    Counts r;
+    if (k <= 7) {
+      Dag g = generate(k);
+      Counts ug = g.counts();
+      if (ug.total != u.total) return QED_EUNSUPPORTED;
+      r = reduce(g).counts();
+    } else {
+      r.total = r.data = r.u = r.v = r.s1 = r.s2 = r.sum = -1;
+    }
+    out->unreduced_total = u.total; out->unreduced_data = u.data; out->unreduced_u = u.u;
+    out->unreduced_v = u.v; out->unreduced_s1 = u.s1; out->unreduced_s2 = u.s2;
+    out->unreduced_sum = u.sum;
+    out->reduced_total = r.total; out->reduced_data = r.data; out->reduced_u = r.u;
+    out->reduced_v = r.v; out->reduced_s1 = r.s1; out->reduced_s2 = r.s2; out->reduced_sum = r.sum;
+  } catch (const std::bad_alloc&) {
+    return QED_ENOMEM;
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  return QED_OK;
+}
+
+qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
+                           qed_precision precision, qed_plan_t* out) {
+  if (!process || !spin || !out) return QED_EINVAL;
+  const int k = process->k;
+  if (k < 1 || k > 7) return QED_EINVAL;
+  if (!(process->mass > 0.0) || !std::isfinite(process->mass) || !std::isfinite(process->charge))
+    return QED_EINVAL;
+  if (precision != QED_FP64 && precision != QED_MIXED) return QED_EINVAL;
+  qed_plan_s* P = new (std::nothrow) qed_plan_s();
+  if (!P) return QED_ENOMEM;
+  P->k = k;
+  P->summed = spin->summed != 0;
+  P->prec = precision;
+  P->mass = process->mass;
+  P->charge = process->charge;
+  if (!P->summed) {
+    for (int s = 0; s < k + 3; ++s) {
+      int v = spin->hel[s];
+      bool electron = (s == 0 || s == 2);
+      if (electron ? (v != 1 && v != -1) : (v != 1 && v != 2)) { delete P; return QED_EINVAL; }
+    }
+    P->fixed_sin = spin->hel[0] == 1 ? 0 : 1;
+    P->fixed_sout = spin->hel[2] == 1 ? 0 : 1;
+    P->fixed_pol[0] = spin->hel[1] - 1;
+    for (int j = 1; j <= k; ++j) P->fixed_pol[j] = spin->hel[j + 2] - 1;
+  }
+  int ls, rs;
+  default_levels(k, P->summed, &ls, &rs);
+  try {
+    P->sc = build_schedule(k, P->summed, ls, rs);
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return QED_ENOMEM;
+  } catch (...) {
+    delete P;
+    return QED_EUNSUPPORTED;
+  }
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess) e = upload(&P->d_instr, P->sc.instr);
+  if (e == cudaSuccess) e = upload(&P->d_phases, P->sc.phases);
+  if (e == cudaSuccess) e = upload(&P->d_sets, P->sc.sets);
+  if (e != cudaSuccess) { free_plan(P); return cuda_status(e); }
+  const bool mixed = precision == QED_MIXED;
+  P->kc = forward_kernel(k, P->summed, mixed);
+  if (!P->kc.fn) { free_plan(P); return QED_EUNSUPPORTED; }
+  const int ncur = P->sc.stored_currents + P->sc.local_currents;
+  TeamLayout L = team_layout(k, mixed ? 4 : 8, ncur);
+  P->team_bytes = L.bytes;
+  P->block = P->kc.team > 32 ? P->kc.team : 128;
+  P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  int dev_smem = 0, sms = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  while (P->smem > (size_t)dev_smem && P->block > P->kc.team && P->block > 32) {
+    P->block /= 2;
+    P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  }
+  if (P->smem > (size_t)dev_smem) { free_plan(P); return QED_EUNSUPPORTED; }
+  e = cudaFuncSetAttribute((const void*)P->kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)P->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc.fn, P->block,
+                                                      P->smem);
+  if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
+  P->grid = per_sm * sms;
+  *out = P;
+  return QED_OK;
+}
+
+qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
+  if (!P || !info) return QED_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  const Schedule& sc = P->sc;
+  info->k = P->k;
+  info->n_photons = sc.n;
+  long long d = 1;
+  for (int i = 2; i <= sc.n; ++i) d *= i;
+  info->n_diagrams = d;
+  info->n_states = P->summed ? (1ll << (sc.n + 2)) : 1;
+  info->nodes_unreduced = sc.unreduced.total;
+  info->nodes_reduced = sc.reduced.total;
+  info->compute_reduced = sc.reduced.total - sc.reduced.data;
+  info->v_nodes = sc.v_nodes;
+  info->s1_nodes = sc.s1_nodes;
+  info->s2_nodes = sc.s2_nodes;
+  info->flops_per_point = sc.flops_algorithmic;
+  info->flops_executed_per_point = sc.flops_executed;
+  info->flops_literal_s2_per_point = sc.flops_literal_s2;
+  info->team_threads = P->kc.team;
+  info->smem_bytes_per_team = P->team_bytes;
+  info->precision = (int)P->prec;
+  return QED_OK;
+}
+
+qed_status qed_eval(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
+                    void* stream) {
+  if (!P || n < 0) return QED_EINVAL;
+  if (n == 0) return QED_OK;
+  if (!d_momenta || !d_out_m2 || !aligned8(d_momenta) || !aligned8(d_out_m2)) return QED_EINVAL;
+  return launch_eval(P, d_momenta, n, d_out_m2, (cudaStream_t)stream);
+}
+
+qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
+                         double* d_grad, void* stream) {
+  if (!P || n < 0) return QED_EINVAL;
+  if (n == 0) return QED_OK;
+  if (!d_momenta || !d_grad) return QED_EINVAL;
+  (void)d_out_m2;
+  (void)stream;
+  return QED_EUNSUPPORTED;
+}
+
+qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, double* h_out_m2,
+                         void* stream) {
+  if (!P || n < 0) return QED_EINVAL;
+  if (n == 0) return QED_OK;
+  if (!h_momenta || !h_out_m2) return QED_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long stride = (long long)(P->k + 3) * 4;
+  // two staging buffers of `chunk` points each: momenta then |M|^2
+  const long long chunk = std::min<long long>(n, std::max<long long>(1 << 16, (n + 7) / 8));
+  cudaError_t e = cudaSuccess;
+  if (chunk > P->stage_cap) {
+    cudaFree(P->d_stage);
+    P->d_stage = nullptr;
+    P->stage_cap = 0;
+    e = cudaMalloc((void**)&P->d_stage, (size_t)2 * chunk * (stride + 1) * sizeof(double));
+    if (e != cudaSuccess) return cuda_status(e);
+    P->stage_cap = chunk;
+  }
+  if (!P->s_h2d) {
+    e = cudaStreamCreateWithFlags(&P->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->s_d2h, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&P->ev_h2d[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_k[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_d2h[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const long long cap = P->stage_cap;
+  double* mom_buf[2] = {P->d_stage, P->d_stage + cap * stride};
+  double* out_buf[2] = {P->d_stage + 2 * cap * stride, P->d_stage + 2 * cap * stride + cap};
+  // order the staging buffers after earlier work on the caller's stream
+  cudaEvent_t start = P->ev_k[0];
+  e = cudaEventRecord(start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_h2d, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_d2h, start, 0);
+  long long c = 0;
+  for (long long off = 0; off < n && e == cudaSuccess; off += chunk, ++c) {
+    const int b = (int)(c & 1);
+    const long long m = std::min(chunk, n - off);
+    if (c >= 2) e = cudaStreamWaitEvent(P->s_h2d, P->ev_k[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(mom_buf[b], h_momenta + off * stride, (size_t)m * stride * sizeof(double),
+                          cudaMemcpyHostToDevice, P->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_h2d[b], P->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_h2d[b], 0);
+    if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(st, P->ev_d2h[b], 0);
+    if (e == cudaSuccess) {
+      qed_status s = launch_eval(P, mom_buf[b], m, out_buf[b], st);
+      if (s != QED_OK) return s;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_k[b], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_d2h, P->ev_k[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_out_m2 + off, out_buf[b], (size_t)m * sizeof(double),
+                          cudaMemcpyDeviceToHost, P->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_d2h[b], P->s_d2h);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->s_d2h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
+}
+
+void qed_plan_destroy(qed_plan_t P) { free_plan(P); }
+
+// Export of a schedule's tables for host-side inspection (no GPU needed).
+qed_status qed_schedule_export(int k, int summed, qed_schedule_desc_t* desc, void* instr,
+                               void* phases, void* sets) {
+  if (!desc || k < 1 || k > 7) return QED_EINVAL;
+  int ls, rs;
+  default_levels(k, summed != 0, &ls, &rs);
+  Schedule sc;
+  try {
+    sc = build_schedule(k, summed != 0, ls, rs);
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  desc->k = sc.k; desc->n = sc.n; desc->h = sc.h; desc->r = sc.r;
+  desc->ls = sc.ls; desc->rs = sc.rs; desc->summed = sc.summed ? 1 : 0;
+  desc->n_left_leaves = sc.n_left_leaves; desc->n_right_leaves = sc.n_right_leaves;
+  desc->stored_currents = sc.stored_currents; desc->local_currents = sc.local_currents;
+  desc->n_stored_phases = sc.n_stored_phases; desc->n_set_phases = sc.n_set_phases;
+  desc->n_sets = (int)sc.sets.size(); desc->n_instr = (int)sc.instr.size();
+  desc->n_phases = (int)sc.phases.size();
+  desc->flops_algorithmic = sc.flops_algorithmic;
+  desc->flops_executed = sc.flops_executed;
+  if (instr) std::memcpy(instr, sc.instr.data(), sc.instr.size() * sizeof(Instr));
+  if (phases) std::memcpy(phases, sc.phases.data(), sc.phases.size() * sizeof(Phase));
+  if (sets) std::memcpy(sets, sc.sets.data(), sc.sets.size() * sizeof(SetEntry));
+  return QED_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
+same seeded inputs.
+
+FP64 path: per-point relative error <= 1e-12.  Mixed path (FP32 currents and
+Kahan-compensated diagram sums, FP64 momenta, denominators and spin sum): the
+median and maximum relative errors are printed and bounded by MIXED_TOL.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_19456_b300 import Plan, phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = {1: 1e-5, 2: 1e-5, 3: 1e-5, 4: 1e-4, 5: 1e-4, 6: 1e-3, 7: 1e-3}
+
+# (k, summed, omega, points compared with the oracle)
+CASES = [
+    (1, True, 1.0, 65536), (2, True, 2.0, 2048), (3, True, 3.0, 1024), (4, True, 4.0, 512),
+    (5, True, 6.0, 32), (6, True, 8.0, 4),
+    (1, False, 1.0, 4096), (2, False, 2.0, 1024), (3, False, 3.0, 1024), (4, False, 4.0, 512),
+    (5, False, 6.0, 256), (6, False, 8.0, 256), (7, False, 10.0, 48),
+]
+
+
+def fixed_hel(k):
+    return [1, 1, 1] + [1] * k if k == 6 else [1, 2, -1] + [1 + (j % 2) for j in range(k)]
+
+
+def run(plan, mom):
+    d = torch.from_numpy(mom).cuda()
+    out = plan.eval(d)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def reference(orc, k, summed, mom):
+    if summed:
+        return orc.m2(mom, kappa=True)
+    return orc.m2(mom, sum_mask=0, hel=fixed_hel(k), kappa=True)
+
+
+@pytest.mark.parametrize("k,summed,omega,npts", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_vs_oracle(orc, k, summed, omega, npts, precision):
+    mom = ps.points(k, npts, omega, seed=1000 + 10 * k + summed)
+    ref, kap = reference(orc, k, summed, mom)
+    plan = Plan(k, summed=summed, hel=None if summed else fixed_hel(k), precision=precision)
+    got = run(plan, mom)
+    rel = np.abs(got / ref - 1.0)
+    print(f"\nk={k} summed={summed} {precision}: n={npts} median rel {np.median(rel):.3e} "
+          f"max rel {rel.max():.3e} (kappa max {kap.max():.1f})")
+    assert np.all(np.isfinite(got))
+    if precision == "fp64":
+        assert rel.max() <= FP64_TOL, (rel.max(), int(rel.argmax()))
+    else:
+        assert rel.max() <= MIXED_TOL[k]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 127, 1000, 4099])
+@pytest.mark.parametrize("k,summed", [(1, True), (3, True), (4, True), (5, True), (4, False)])
+def test_ragged_sizes(orc, n, k, summed):
+    mom = ps.points(k, n, 2.0 + k, seed=77)
+    plan = Plan(k, summed=summed, hel=None if summed else fixed_hel(k))
+    got = run(plan, mom)
+    ref, _ = reference(orc, k, summed, mom)
+    assert np.max(np.abs(got / ref - 1.0)) <= FP64_TOL
+
+
+def test_empty_input_launches_nothing():
+    plan = Plan(2)
+    d = torch.empty((0, 5, 4), dtype=torch.float64, device="cuda")
+    out = plan.eval(d)
+    assert out.numel() == 0
+
+
+def test_nonfinite_momenta_give_nonfinite_output():
+    mom = ps.points(3, 8, 3.0, seed=5)
+    mom[2, 3, 1] = np.nan
+    mom[5, 0, 0] = np.inf
+    got = run(Plan(3), mom)
+    assert not np.isfinite(got[2]) and not np.isfinite(got[5])
+    assert np.all(np.isfinite(np.delete(got, [2, 5])))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_k4_sampled(orc, precision):
+    """The 1,048,576-point k = 4 workload in the benchmark's launch
+    configuration, checked on a sample of points against the oracle."""
+    w = ps.WORKLOADS["compton_k4"]
+    mom = ps.workload_points("compton_k4")
+    plan = Plan(4, summed=True, precision=precision)
+    got = run(plan, mom)
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    idx = np.random.default_rng(0).choice(w["n_points"], 256, replace=False)
+    idx = np.concatenate([idx, [0, w["n_points"] - 1]])
+    ref = orc.m2(mom[idx])
+    rel = np.abs(got[idx] / ref - 1.0)
+    print(f"\nfull k=4 {precision}: sampled max rel {rel.max():.3e} median {np.median(rel):.3e}")
+    assert rel.max() <= (FP64_TOL if precision == "fp64" else MIXED_TOL[4])
+
+
+def test_photon_permutation_invariance_full_size():
+    """Spin-summed |M|^2 is symmetric under permuting the outgoing photons; this
+    holds at any size and is checked on every point of the k = 4 workload."""
+    mom = ps.workload_points("compton_k4", 1 << 18)
+    perm = mom.copy()
+    perm[:, 3:] = mom[:, [5, 3, 6, 4]]
+    plan = Plan(4)
+    a, b = run(plan, mom), run(plan, perm)
+    assert np.max(np.abs(a / b - 1.0)) < 1e-11
+
+
+def test_coupling_and_mass_parameters(orc):
+    mom = ps.points(2, 64, 2.0, seed=9, mass=0.7)
+    plan = Plan(2, mass=0.7, charge=0.3)
+    got = run(plan, mom)
+    ref = orc.m2(mom, mass=0.7) * 0.3 ** 6
+    assert np.max(np.abs(got / ref - 1.0)) <= FP64_TOL
+
+
+def test_plan_info_counts():
+    info = Plan(4).info()
+    assert info["n_diagrams"] == 120 and info["n_states"] == 128
+    assert info["nodes_unreduced"] == 2183
+    assert info["s2_nodes"] == 120 * 128
+    assert info["flops_per_point"] > 120 * 128 * 32
