@@ -186,6 +186,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 path (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+                    help="time one precision only (profiling runs)")
+    ap.add_argument("--n-points", type=int, default=None,
+                    help="override the workload's point count (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args, args.workload)
@@ -203,7 +208,8 @@ def main():
     from paper_2511_19456_b300 import Plan, measure_fma_peak
 
     w = ps.WORKLOADS[args.workload]
-    k, n = w["k"], w["n_points"]
+    k = w["k"]
+    n = args.n_points or w["n_points"]
     mom = ps.points(k, n, w["omega"], w["seed"] + 7919 * rank)
     d_mom = torch.from_numpy(mom).cuda()
     out = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -214,7 +220,10 @@ def main():
     launches = 0
     clocks = None
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else args.steps
-    for prec, steps in (("mixed", args.steps), ("fp64", fp64_steps)):
+    legs = [("mixed", args.steps), ("fp64", fp64_steps)]
+    if args.only:
+        legs = [l for l in legs if l[0] == args.only]
+    for prec, steps in legs:
         plan = Plan(k, summed=w["summed"], hel=hel, precision=prec)
         info = plan.info()
         with ClockSampler(local) as cs:
@@ -237,26 +246,42 @@ def main():
         if prec == "mixed":
             clocks = cs.summary()
 
+    if args.only:
+        # profiling run: one precision, no end-to-end leg, a short line
+        r = res[args.only]
+        if rank == 0:
+            print(json.dumps({"profile_run": args.only, "workload": args.workload, "n_points": n,
+                              "ms_per_step": r["ms_per_step"], "value": r["value"],
+                              "roofline": r["roofline"]}), flush=True)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
     # measured FMA-chain peaks (context for the derived peaks above)
     measured = {"fp32_tflops": measure_fma_peak("mixed"), "fp64_tflops": measure_fma_peak("fp64")}
 
     # end to end through the public API on pinned host buffers
-    plan = res["mixed"]["plan"]
-    h_mom = torch.from_numpy(mom).pin_memory()
-    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        plan.eval_host(h_mom, h_out)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        plan.eval_host(h_mom, h_out)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    chunk = min(n, max(1 << 16, (n + 7) // 8))
-    launches += args.steps * math.ceil(n / chunk)
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e = None
+    if not args.no_e2e:
+        plan = res["mixed"]["plan"]
+        h_mom = torch.from_numpy(mom).pin_memory()
+        h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            plan.eval_host(h_mom, h_out)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.eval_host(h_mom, h_out)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        chunk = min(n, max(1 << 16, (n + 7) // 8))
+        launches += args.steps * math.ceil(n / chunk)
+        if ws > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": n * ws / e2e_s, "unit": "points/s",
+               "h2d_bytes_per_step": int(h_mom.numel() * 8),
+               "d2h_bytes_per_step": int(h_out.numel() * 8)}
 
     if rank != 0:
         if ws > 1:
@@ -287,9 +312,7 @@ def main():
                  "steps": fp64_steps, "roofline": fp64["roofline"], "clocks": fp64["clocks"]},
         "speedup_mixed_vs_fp64": mixed["value"] / fp64["value"],
         "peaks_measured_fma_chain": measured,
-        "e2e": {"value": n * ws / e2e_s, "unit": "points/s",
-                "h2d_bytes_per_step": int(h_mom.numel() * 8),
-                "d2h_bytes_per_step": int(h_out.numel() * 8)},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -1,9 +1,16 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
 same seeded inputs.
 
-FP64 path: per-point relative error <= 1e-12.  Mixed path (FP32 currents and
-Kahan-compensated diagram sums, FP64 momenta, denominators and spin sum): the
-median and maximum relative errors are printed and bounded by MIXED_TOL.
+Tolerances, per point, with kappa = sqrt(sum_l (sum_d |A_d|)^2 / sum_l |M_l|^2)
+the oracle's measure of cancellation among the diagrams:
+* FP64 path: relative error <= max(1e-12, 64 u64 kappa), u64 = 2^-53.  Each
+  diagram carries rounding error of a few u64 |A_d| in any FP64 evaluation
+  (the oracle's included), so where kappa exceeds ~1e2 the 1e-12 target is
+  replaced by the rounding bound.
+* Mixed path (FP32 currents, Kahan-compensated diagram sums; FP64 momenta,
+  denominators, spin sum): relative error <= 4 (2n-1) u32 kappa, u32 = 2^-24,
+  from 2n-1 rounded matrix-vector steps per diagram.  Median and maximum are
+  printed.
 """
 import math
 
@@ -16,7 +23,16 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-MIXED_TOL = {1: 1e-5, 2: 1e-5, 3: 1e-5, 4: 1e-4, 5: 1e-4, 6: 1e-3, 7: 1e-3}
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def fp64_tol(kappa):
+    return np.maximum(FP64_TOL, 64 * U64 * kappa)
+
+
+def mixed_tol(k, kappa):
+    return 4 * (2 * (k + 1) - 1) * U32 * np.maximum(kappa, 1.0)
 
 # (k, summed, omega, points compared with the oracle)
 CASES = [
@@ -55,10 +71,9 @@ def test_parity_vs_oracle(orc, k, summed, omega, npts, precision):
     print(f"\nk={k} summed={summed} {precision}: n={npts} median rel {np.median(rel):.3e} "
           f"max rel {rel.max():.3e} (kappa max {kap.max():.1f})")
     assert np.all(np.isfinite(got))
-    if precision == "fp64":
-        assert rel.max() <= FP64_TOL, (rel.max(), int(rel.argmax()))
-    else:
-        assert rel.max() <= MIXED_TOL[k]
+    tol = fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)
+    bad = np.nonzero(rel > tol)[0]
+    assert bad.size == 0, (bad[:5], rel[bad[:5]], kap[bad[:5]])
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 127, 1000, 4099])
@@ -67,8 +82,8 @@ def test_ragged_sizes(orc, n, k, summed):
     mom = ps.points(k, n, 2.0 + k, seed=77)
     plan = Plan(k, summed=summed, hel=None if summed else fixed_hel(k))
     got = run(plan, mom)
-    ref, _ = reference(orc, k, summed, mom)
-    assert np.max(np.abs(got / ref - 1.0)) <= FP64_TOL
+    ref, kap = reference(orc, k, summed, mom)
+    assert np.all(np.abs(got / ref - 1.0) <= fp64_tol(kap))
 
 
 def test_empty_input_launches_nothing():
@@ -98,29 +113,37 @@ def test_full_size_k4_sampled(orc, precision):
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     idx = np.random.default_rng(0).choice(w["n_points"], 256, replace=False)
     idx = np.concatenate([idx, [0, w["n_points"] - 1]])
-    ref = orc.m2(mom[idx])
+    ref, kap = orc.m2(mom[idx], kappa=True)
     rel = np.abs(got[idx] / ref - 1.0)
     print(f"\nfull k=4 {precision}: sampled max rel {rel.max():.3e} median {np.median(rel):.3e}")
-    assert rel.max() <= (FP64_TOL if precision == "fp64" else MIXED_TOL[4])
+    tol = fp64_tol(kap) if precision == "fp64" else mixed_tol(4, kap)
+    assert np.all(rel <= tol)
 
 
-def test_photon_permutation_invariance_full_size():
+def test_photon_permutation_invariance_full_size(orc):
     """Spin-summed |M|^2 is symmetric under permuting the outgoing photons; this
-    holds at any size and is checked on every point of the k = 4 workload."""
-    mom = ps.workload_points("compton_k4", 1 << 18)
+    holds at any size and is checked on every point of the k = 4 workload.
+    The permuted evaluation rounds differently, so the worst points are
+    checked against the oracle's kappa-scaled rounding bound."""
+    mom = ps.workload_points("compton_k4")
     perm = mom.copy()
     perm[:, 3:] = mom[:, [5, 3, 6, 4]]
     plan = Plan(4)
     a, b = run(plan, mom), run(plan, perm)
-    assert np.max(np.abs(a / b - 1.0)) < 1e-11
+    rel = np.abs(a / b - 1.0)
+    print(f"\npermutation: max rel {rel.max():.3e}, fraction > 1e-12: {np.mean(rel > 1e-12):.2e}")
+    assert np.mean(rel > FP64_TOL) < 1e-3
+    worst = np.argsort(rel)[-16:]
+    _, kap = orc.m2(mom[worst], kappa=True)
+    assert np.all(rel[worst] <= 2 * fp64_tol(kap))
 
 
 def test_coupling_and_mass_parameters(orc):
     mom = ps.points(2, 64, 2.0, seed=9, mass=0.7)
     plan = Plan(2, mass=0.7, charge=0.3)
     got = run(plan, mom)
-    ref = orc.m2(mom, mass=0.7) * 0.3 ** 6
-    assert np.max(np.abs(got / ref - 1.0)) <= FP64_TOL
+    ref, kap = orc.m2(mom, mass=0.7, kappa=True)
+    assert np.all(np.abs(got / (ref * 0.3 ** 6) - 1.0) <= fp64_tol(kap))
 
 
 def test_plan_info_counts():
