@@ -123,8 +123,10 @@ def test_full_size_k4_sampled(orc, precision):
 def test_photon_permutation_invariance_full_size(orc):
     """Spin-summed |M|^2 is symmetric under permuting the outgoing photons; this
     holds at any size and is checked on every point of the k = 4 workload.
-    The permuted evaluation rounds differently, so the worst points are
-    checked against the oracle's kappa-scaled rounding bound."""
+    Permuting the slots changes the order in which propagator momenta are
+    summed, so near-on-shell lines round differently (the input's own
+    conditioning, not the kernel's): at the worst points the GPU must agree
+    with the oracle on both the original and the permuted input."""
     mom = ps.workload_points("compton_k4")
     perm = mom.copy()
     perm[:, 3:] = mom[:, [5, 3, 6, 4]]
@@ -132,10 +134,12 @@ def test_photon_permutation_invariance_full_size(orc):
     a, b = run(plan, mom), run(plan, perm)
     rel = np.abs(a / b - 1.0)
     print(f"\npermutation: max rel {rel.max():.3e}, fraction > 1e-12: {np.mean(rel > 1e-12):.2e}")
-    assert np.mean(rel > FP64_TOL) < 1e-3
+    assert np.mean(rel > FP64_TOL) < 1e-3 and rel.max() < 1e-9
     worst = np.argsort(rel)[-16:]
-    _, kap = orc.m2(mom[worst], kappa=True)
-    assert np.all(rel[worst] <= 2 * fp64_tol(kap))
+    ra, ka = orc.m2(mom[worst], kappa=True)
+    rb, kb = orc.m2(perm[worst], kappa=True)
+    assert np.all(np.abs(a[worst] / ra - 1.0) <= fp64_tol(ka))
+    assert np.all(np.abs(b[worst] / rb - 1.0) <= fp64_tol(kb))
 
 
 def test_coupling_and_mass_parameters(orc):
