@@ -16,33 +16,43 @@
 namespace qed {
 
 // ------------------------------------------------------------ U: states
-// Helicity spinor u(p, h) (FP64): u = (sqrt(E+m) chi, h sqrt(E-m) chi), with
-// chi_+ = (|p|+pz, px + i py)/sqrt(2|p|(|p|+pz)), chi_- = (-px + i py,
-// |p|+pz)/sqrt(2|p|(|p|+pz)); |p| = 0 uses the z axis, |p|+pz = 0 gives
-// chi_+ = (0, 1), chi_- = (-1, 0).  bar: ubar = u^dagger gamma^0.
-__device__ __forceinline__ void make_spinor(const double* p, int hbit, double m, bool bar,
-                                            double out[8]) {
-  const double px = p[1], py = p[2], pz = p[3];
-  const double ap = sqrt(px * px + py * py + pz * pz);
-  double c0r, c0i, c1r, c1i;
-  if (ap == 0.0) {
-    c0r = hbit ? 0.0 : 1.0; c0i = 0.0; c1r = hbit ? 1.0 : 0.0; c1i = 0.0;
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+// Helicity spinor u(p, h) in precision T from the FP64 momentum p:
+// u = (sqrt(E+m) chi, h sqrt(E-m) chi), chi_+ = (|p|+pz, px + i py)/N,
+// chi_- = (-px + i py, |p|+pz)/N, N = sqrt(2|p|(|p|+pz)); |p| = 0 uses the
+// z axis, |p|+pz = 0 gives chi_+ = (0, 1), chi_- = (-1, 0).
+// bar: ubar = u^dagger gamma^0.  E +- m are formed in FP64.  In FP32, |p|+pz
+// is formed as (px^2 + py^2)/(|p| - pz) when pz < 0 (the same quantity
+// without the cancellation near the -z axis).
+template <typename T>
+__device__ __forceinline__ void make_spinor(const double* p, int hbit, double m, bool bar, T out[8]) {
+  const T px = (T)p[1], py = (T)p[2], pz = (T)p[3];
+  const T pt2 = px * px + py * py;
+  const T ap = sqrt_t(pt2 + pz * pz);
+  T c0r, c0i, c1r, c1i;
+  if (ap == (T)0) {
+    c0r = hbit ? (T)0 : (T)1; c0i = (T)0; c1r = hbit ? (T)1 : (T)0; c1i = (T)0;
   } else {
-    const double apz = ap + pz;
-    if (apz == 0.0) {
-      c0r = hbit ? -1.0 : 0.0; c0i = 0.0; c1r = hbit ? 0.0 : 1.0; c1i = 0.0;
+    T apz;
+    if constexpr (sizeof(T) == 8) apz = ap + pz;
+    else apz = pz >= (T)0 ? ap + pz : pt2 / (ap - pz);
+    if (apz == (T)0) {
+      c0r = hbit ? (T)-1 : (T)0; c0i = (T)0; c1r = hbit ? (T)0 : (T)1; c1i = (T)0;
     } else {
-      const double nrm = sqrt(2.0 * ap * apz);
-      if (!hbit) { c0r = apz / nrm; c0i = 0.0; c1r = px / nrm; c1i = py / nrm; }
-      else       { c0r = -px / nrm; c0i = py / nrm; c1r = apz / nrm; c1i = 0.0; }
+      const T nrm = sqrt_t((T)2 * ap * apz);
+      if (!hbit) { c0r = apz / nrm; c0i = (T)0; c1r = px / nrm; c1i = py / nrm; }
+      else       { c0r = -px / nrm; c0i = py / nrm; c1r = apz / nrm; c1i = (T)0; }
     }
   }
-  const double a = sqrt(p[0] + m);
-  const double bb = p[0] - m;
-  double b = bb > 0.0 ? sqrt(bb) : 0.0;
+  const T a = sqrt_t((T)(p[0] + m));
+  const T bb = (T)(p[0] - m);
+  T b = bb > (T)0 ? sqrt_t(bb) : (T)0;
   if (hbit) b = -b;
-  double u[8] = {a * c0r, a * c0i, a * c1r, a * c1i, b * c0r, b * c0i, b * c1r, b * c1i};
+  const T u[8] = {a * c0r, a * c0i, a * c1r, a * c1i, b * c0r, b * c0i, b * c1r, b * c1i};
   if (!bar) {
+#pragma unroll
     for (int i = 0; i < 8; ++i) out[i] = u[i];
   } else {
     // conjugate, then flip the lower two components (gamma^0)
@@ -52,27 +62,30 @@ __device__ __forceinline__ void make_spinor(const double* p, int hbit, double m,
 }
 
 // Real linear polarisation 3-vector (eps^0 = 0) of a photon with momentum k.
-__device__ __forceinline__ void make_pol(const double* k, int pbit, double e[3]) {
-  const double kx = k[1], ky = k[2], kz = k[3];
-  const double kt2 = kx * kx + ky * ky;
-  if (kt2 == 0.0) {
-    e[0] = pbit ? 0.0 : 1.0; e[1] = pbit ? 1.0 : 0.0; e[2] = 0.0;
+template <typename T>
+__device__ __forceinline__ void make_pol(const double* k, int pbit, T e[3]) {
+  const T kx = (T)k[1], ky = (T)k[2], kz = (T)k[3];
+  const T kt2 = kx * kx + ky * ky;
+  if (kt2 == (T)0) {
+    e[0] = pbit ? (T)0 : (T)1; e[1] = pbit ? (T)1 : (T)0; e[2] = (T)0;
     return;
   }
-  const double kt = sqrt(kt2);
+  const T kt = sqrt_t(kt2);
   if (!pbit) {
-    const double den = sqrt(kt2 + kz * kz) * kt;
+    const T den = sqrt_t(kt2 + kz * kz) * kt;
     e[0] = kx * kz / den; e[1] = ky * kz / den; e[2] = -kt2 / den;
   } else {
-    e[0] = -ky / kt; e[1] = kx / kt; e[2] = 0.0;
+    e[0] = -ky / kt; e[1] = kx / kt; e[2] = (T)0;
   }
 }
 
 // Propagator of the line carrying photon set `mask`: Q = p + sum c_j k_j
 // over the set in ascending slot order, D = Q0^2 - Qx^2 - Qy^2 - Qz^2 - m^2
-// with every product rounded separately.  Writes (Q0+m)/D, (Q0-m)/D, Q/D.
-__device__ __forceinline__ void make_prop(const double* mom, int n, unsigned mask, double m,
-                                          double out[5]) {
+// with every product rounded separately, all in FP64.  Writes (Q0+m)/D,
+// (Q0-m)/D, Q/D in precision T (for T = float the quotients are formed in
+// FP32 from the FP64 numerators and denominator).
+template <typename T>
+__device__ __forceinline__ void make_prop(const double* mom, int n, unsigned mask, double m, T out[5]) {
   double q0 = mom[0], q1 = mom[1], q2 = mom[2], q3 = mom[3];
   for (int j = 0; j < n; ++j) {
     if (!(mask & (1u << j))) continue;
@@ -85,12 +98,21 @@ __device__ __forceinline__ void make_prop(const double* mom, int n, unsigned mas
   D = __dsub_rn(D, __dmul_rn(q2, q2));
   D = __dsub_rn(D, __dmul_rn(q3, q3));
   D = __dsub_rn(D, __dmul_rn(m, m));
-  const double inv = 1.0 / D;
-  out[0] = (q0 + m) * inv;
-  out[1] = (q0 - m) * inv;
-  out[2] = q1 * inv;
-  out[3] = q2 * inv;
-  out[4] = q3 * inv;
+  if constexpr (sizeof(T) == 8) {
+    const double inv = 1.0 / D;
+    out[0] = (q0 + m) * inv;
+    out[1] = (q0 - m) * inv;
+    out[2] = q1 * inv;
+    out[3] = q2 * inv;
+    out[4] = q3 * inv;
+  } else {
+    const float inv = 1.0f / (float)D;
+    out[0] = (float)(q0 + m) * inv;
+    out[1] = (float)(q0 - m) * inv;
+    out[2] = (float)q1 * inv;
+    out[3] = (float)q2 * inv;
+    out[4] = (float)q3 * inv;
+  }
 }
 
 // ------------------------------------------------- 2x2 Pauli products
@@ -161,12 +183,23 @@ QED_HD void dot_acc(const R* Rw, const R* Lc, R& re, R& im) {
   }
 }
 
-// Kahan-compensated add of x into (s, c); the represented value is s - c.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = __fsub_rn(x, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
+// Error-free FP32 transformations (Knuth TwoSum; TwoProd through fma).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Adds (hi - c)^2 to the float-float accumulator (acc_hi, acc_lo); hi - c is a
+// Kahan-compensated value with |c| far below ulp(hi).
+__device__ __forceinline__ void add_square_ff(float hi, float c, float& acc_hi, float& acc_lo) {
+  const float p = __fmul_rn(hi, hi);
+  const float e = __fmaf_rn(hi, hi, -p);           // hi^2 = p + e exactly
+  const float t = __fmaf_rn(-2.0f * hi, c, e);     // + 2 hi (-c); c^2 is below rounding
+  float s, err;
+  two_sum_f(acc_hi, p, s, err);
+  acc_hi = s;
+  acc_lo = __fadd_rn(acc_lo, __fadd_rn(err, t));
 }
 
 // pext: gather the bits of v selected by mask into the low bits.

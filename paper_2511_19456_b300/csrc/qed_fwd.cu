@@ -50,6 +50,37 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
   return v;
 }
 
+// Currents live in shared memory component-major: a node whose current has
+// nv spin variants occupies 4*nv complex slots starting at 4*base, component
+// c of variant v at slot 4*base + c*nv + v.  Threads that work on
+// neighbouring variants then touch neighbouring 8- (FP32) or 16-byte (FP64)
+// words, free of bank conflicts.
+template <typename Real> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+// contiguous layout: variant v of node base at 8*(base+v) reals
+__device__ __forceinline__ void load_cur(const float* cur, int base, int nv, int v, float x[8]) {
+  const float4* q = reinterpret_cast<const float4*>(cur + (size_t)(base + v) * 8);
+  const float4 a = q[0], b = q[1];
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void store_cur(float* cur, int base, int nv, int v, const float x[8]) {
+  float4* q = reinterpret_cast<float4*>(cur + (size_t)(base + v) * 8);
+  q[0] = make_float4(x[0], x[1], x[2], x[3]);
+  q[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+__device__ __forceinline__ void load_cur(const double* cur, int base, int nv, int v, double x[8]) {
+  const double2* q = reinterpret_cast<const double2*>(cur + (size_t)(base + v) * 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { const double2 a = q[i]; x[2 * i] = a.x; x[2 * i + 1] = a.y; }
+}
+__device__ __forceinline__ void store_cur(double* cur, int base, int nv, int v, const double x[8]) {
+  double2* q = reinterpret_cast<double2*>(cur + (size_t)(base + v) * 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = make_double2(x[2 * i], x[2 * i + 1]);
+}
+// External spinors: 8 contiguous reals.
 template <typename Real>
 __device__ __forceinline__ void load8(const Real* p, Real x[8]) {
 #pragma unroll
@@ -69,7 +100,24 @@ __device__ __forceinline__ Instr ld_instr(const Instr* p) {
   return in;
 }
 
-// One V (+S1) instruction for spin variant v.
+// Vertex (+ propagation) of one input current x for photon polarisation pol,
+// stored as variant v of the instruction's node.
+template <typename Real>
+__device__ __forceinline__ void vertex_store(const Instr& in, const Real x[8], int pol, int v, int nv,
+                                             const Real* s_q, const Real* s_eps, Real* s_cur) {
+  const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
+  const Real ev[3] = {e3[0], e3[1], e3[2]};
+  Real y[8], z[8];
+  if (in.side == 0) vertex_col(ev, x, y); else vertex_row(ev, x, y);
+  if (in.post) {
+    const Real* P = s_q + in.post * 5;
+    if (in.side == 0) prop_col(P, y, z); else prop_row(P, y, z);
+    store_cur(s_cur, in.dst, nv, v, z);
+  } else {
+    store_cur(s_cur, in.dst, nv, v, y);
+  }
+}
+
 template <bool SUMMED, typename Real>
 __device__ __forceinline__ void apply_instr(const Instr& in, int v, const KParams& p,
                                             const Real* s_q, const Real* s_eps,
@@ -83,23 +131,14 @@ __device__ __forceinline__ void apply_instr(const Instr& in, int v, const KParam
     pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
     vp = 0;
   }
-  Real x[8], y[8];
+  Real x[8];
   if (in.src < 0) {
     const int e = SUMMED ? vp : (in.side == 0 ? p.fixed_sin : p.fixed_sout);
     load8(s_spin + (in.side * 2 + e) * 8, x);
   } else {
-    load8(s_cur + (size_t)(in.src + vp) * 8, x);
+    load_cur(s_cur, in.src, 0, vp, x);
   }
-  const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
-  Real ev[3] = {e3[0], e3[1], e3[2]};
-  if (in.side == 0) vertex_col(ev, x, y); else vertex_row(ev, x, y);
-  if (in.post) {
-    const Real* P = s_q + in.post * 5;
-    if (in.side == 0) prop_col(P, y, x); else prop_row(P, y, x);
-    store8(s_cur + (size_t)(in.dst + v) * 8, x);
-  } else {
-    store8(s_cur + (size_t)(in.dst + v) * 8, y);
-  }
+  vertex_store(in, x, pol, v, 0, s_q, s_eps, s_cur);
 }
 
 template <int TEAM, bool SUMMED, typename Real>
@@ -138,9 +177,24 @@ template <> struct Acc<double> {
   __device__ __forceinline__ double vre() const { return re; }
   __device__ __forceinline__ double vim() const { return im; }
 };
+// Kahan-compensated: the represented value is (re - cre, im - cim).  A group of
+// diagrams is accumulated by an FMA chain that starts from -c (the first
+// step of a Kahan update), then committed with the remaining two steps.
 template <> struct Acc<float> {
   float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
-  __device__ __forceinline__ void add(float r, float i) { kahan_add(re, cre, r); kahan_add(im, cim, i); }
+  __device__ __forceinline__ void start(float& yr, float& yi) const { yr = -cre; yi = -cim; }
+  __device__ __forceinline__ void commit(float yr, float yi) {
+    const float tr = __fadd_rn(re, yr), ti = __fadd_rn(im, yi);
+    cre = __fsub_rn(__fsub_rn(tr, re), yr);
+    cim = __fsub_rn(__fsub_rn(ti, im), yi);
+    re = tr;
+    im = ti;
+  }
+  __device__ __forceinline__ void add(float r, float i) {
+    float yr, yi;
+    start(yr, yi);
+    commit(__fadd_rn(yr, r), __fadd_rn(yi, i));
+  }
   __device__ __forceinline__ double vre() const { return (double)re - (double)cre; }
   __device__ __forceinline__ double vim() const { return (double)im - (double)cim; }
 };
@@ -158,7 +212,8 @@ qed_fwd_kernel(const KParams p) {
   constexpr int NVR = SUMMED ? (1 << (R + 1)) : 1;
   constexpr int NL = [] { int f = 1; for (int i = 2; i <= H; ++i) f *= i; return f; }();
   constexpr int NR = [] { int f = 1; for (int i = 2; i <= R; ++i) f *= i; return f; }();
-  constexpr int BC = NR >= 2 ? 2 : 1;
+  constexpr int BC = NR >= 2 ? 2 : 1;   // right leaves held in registers
+  constexpr int GA = NL % 2 == 0 ? 2 : 1; // left leaves per compensated step
 
   extern __shared__ __align__(16) unsigned char smem[];
   const TeamLayout L = team_layout(K, (int)sizeof(Real), p.ncur);
@@ -182,32 +237,34 @@ qed_fwd_kernel(const KParams p) {
     for (int i = lane; i < NS * 4; i += TEAM) s_mom[i] = __ldg(p.mom + ptc * (NS * 4) + i);
     team_sync<TEAM>();
 
-    // ---- a2/a3: external states and propagators (FP64)
-    for (int it = lane; it < 4 + 2 * N + NSUB; it += TEAM) {
+    // ---- a3: propagator entries of every photon subset, one subset per
+    // thread (momenta and denominators in FP64)
+    for (int mask = lane; mask < NSUB; mask += TEAM) {
+      Real* d = s_q + mask * 5;
+      Real P[5];
+      if (mask == 0 || mask == (int)ALL) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) P[c] = (Real)0;
+      } else {
+        make_prop<Real>(s_mom, N, (unsigned)mask, p.mass, P);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d[c] = P[c];
+    }
+    // ---- a2: external states u(p, +-), ubar(p', +-), eps_j(pol 1, 2) in
+    // the working precision
+    for (int it = lane; it < 4 + 2 * N; it += TEAM) {
       if (it < 4) {
         const int side = it >> 1, e = it & 1;
-        double s[8];
-        make_spinor(s_mom + (side ? 8 : 0), e, p.mass, side == 1, s);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) s_spin[(side * 2 + e) * 8 + c] = (Real)s[c];
-      } else if (it < 4 + 2 * N) {
-        const int j = (it - 4) >> 1, pb = (it - 4) & 1;
-        double e[3];
-        make_pol(s_mom + 4 * (j == 0 ? 1 : j + 2), pb, e);
-        Real* d = s_eps + (j * 2 + pb) * 4;
-        d[0] = (Real)e[0]; d[1] = (Real)e[1]; d[2] = (Real)e[2]; d[3] = (Real)0;
+        Real s[8];
+        make_spinor<Real>(s_mom + (side ? 8 : 0), e, p.mass, side == 1, s);
+        store8(s_spin + (side * 2 + e) * 8, s);
       } else {
-        const unsigned mask = (unsigned)(it - 4 - 2 * N);
-        Real* d = s_q + mask * 5;
-        if (mask == 0 || mask == ALL) {
-#pragma unroll
-          for (int c = 0; c < 5; ++c) d[c] = (Real)0;
-        } else {
-          double P[5];
-          make_prop(s_mom, N, mask, p.mass, P);
-#pragma unroll
-          for (int c = 0; c < 5; ++c) d[c] = (Real)P[c];
-        }
+        const int j = (it - 4) >> 1, pb = (it - 4) & 1;
+        Real e[3];
+        make_pol<Real>(s_mom + 4 * (j == 0 ? 1 : j + 2), pb, e);
+        Real* d = s_eps + (j * 2 + pb) * 4;
+        d[0] = e[0]; d[1] = e[1]; d[2] = e[2]; d[3] = (Real)0;
       }
     }
     team_sync<TEAM>();
@@ -232,32 +289,40 @@ qed_fwd_kernel(const KParams p) {
         const unsigned c = (unsigned)lane;
         const int vl = (int)pext_bits(c, se.mask, N) << 1;
         const int vr = (int)pext_bits(c, ALL & ~se.mask, N) << 1;
-        const Real* Lb = s_cur + (size_t)(se.leaf_l + vl) * 8;
-        const Real* Rb = s_cur + (size_t)(se.leaf_r + vr) * 8;
+
         for (int b0 = 0; b0 < NR; b0 += BC) {
           Real rw[BC][2][8];
 #pragma unroll
           for (int bb = 0; bb < BC; ++bb)
 #pragma unroll
-            for (int so = 0; so < 2; ++so) load8(Rb + (size_t)((b0 + bb) * NVR + so) * 8, rw[bb][so]);
-          for (int a = 0; a < NL; ++a) {
-            Real lc[2][8];
+            for (int so = 0; so < 2; ++so)
+              load_cur(s_cur, se.leaf_r + (b0 + bb) * NVR, NVR, vr + so, rw[bb][so]);
+          for (int a0 = 0; a0 < NL; a0 += GA) {
+            Real lc[GA][2][8];
 #pragma unroll
-            for (int si = 0; si < 2; ++si) load8(Lb + (size_t)(a * NVL + si) * 8, lc[si]);
+            for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+              for (int si = 0; si < 2; ++si)
+                load_cur(s_cur, se.leaf_l + (a0 + ga) * NVL, NVL, vl + si, lc[ga][si]);
 #pragma unroll
             for (int si = 0; si < 2; ++si)
 #pragma unroll
               for (int so = 0; so < 2; ++so) {
-                Real re = (Real)0, im = (Real)0;
+                if constexpr (sizeof(Real) == 8) {
 #pragma unroll
-                for (int bb = 0; bb < BC; ++bb) {
-                  if constexpr (sizeof(Real) == 8) {
-                    dot_acc(rw[bb][so], lc[si], acc[si * 2 + so].re, acc[si * 2 + so].im);
-                  } else {
-                    re = (Real)0; im = (Real)0;
-                    dot_acc(rw[bb][so], lc[si], re, im);
-                    acc[si * 2 + so].add(re, im);
-                  }
+                  for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+                    for (int bb = 0; bb < BC; ++bb)
+                      dot_acc(rw[bb][so], lc[ga][si], acc[si * 2 + so].re, acc[si * 2 + so].im);
+                } else {
+                  // the GA x BC diagrams of this state in one compensated step
+                  float yr, yi;
+                  acc[si * 2 + so].start(yr, yi);
+#pragma unroll
+                  for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+                    for (int bb = 0; bb < BC; ++bb) dot_acc(rw[bb][so], lc[ga][si], yr, yi);
+                  acc[si * 2 + so].commit(yr, yi);
                 }
               }
           }
@@ -266,14 +331,15 @@ qed_fwd_kernel(const KParams p) {
         for (int q = lane; q < NL * NR; q += TEAM) {
           const int a = q / NR, b = q - a * NR;
           Real lc[8], rw[8];
-          load8(s_cur + (size_t)(se.leaf_l + a) * 8, lc);
-          load8(s_cur + (size_t)(se.leaf_r + b) * 8, rw);
+          load_cur(s_cur, se.leaf_l + a, 1, 0, lc);
+          load_cur(s_cur, se.leaf_r + b, 1, 0, rw);
           if constexpr (sizeof(Real) == 8) {
             dot_acc(rw, lc, acc[0].re, acc[0].im);
           } else {
-            Real re = (Real)0, im = (Real)0;
-            dot_acc(rw, lc, re, im);
-            acc[0].add(re, im);
+            float yr, yi;
+            acc[0].start(yr, yi);
+            dot_acc(rw, lc, yr, yi);
+            acc[0].commit(yr, yi);
           }
         }
       }
@@ -283,11 +349,21 @@ qed_fwd_kernel(const KParams p) {
     // ---- a8/a9: square, spin sum in FP64, store
     double m2;
     if constexpr (SUMMED) {
-      double part = 0.0;
+      double part;
+      if constexpr (sizeof(Real) == 8) {
+        part = 0.0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const double re = acc[i].vre(), im = acc[i].vim();
-        part = fma(re, re, fma(im, im, part));
+        for (int i = 0; i < 4; ++i) part = fma(acc[i].re, acc[i].re, fma(acc[i].im, acc[i].im, part));
+      } else {
+        // squares of the compensated amplitudes, exact to ~2^-48 in
+        // float-float; the sum over the team's states in FP64
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          add_square_ff(acc[i].re, acc[i].cre, hi, lo);
+          add_square_ff(acc[i].im, acc[i].cim, hi, lo);
+        }
+        part = (double)hi + (double)lo;
       }
       m2 = team_sum<TEAM>(part, s_red);
     } else {

@@ -8,9 +8,11 @@ the oracle's measure of cancellation among the diagrams:
   (the oracle's included), so where kappa exceeds ~1e2 the 1e-12 target is
   replaced by the rounding bound.
 * Mixed path (FP32 currents, Kahan-compensated diagram sums; FP64 momenta,
-  denominators, spin sum): relative error <= 4 (2n-1) u32 kappa, u32 = 2^-24,
-  from 2n-1 rounded matrix-vector steps per diagram.  Median and maximum are
-  printed.
+  denominators, spin sum): relative error <= 32 (2n-1) u32 max(kappa, 1),
+  u32 = 2^-24: 2n-1 rounded matrix-vector steps per diagram, each of which
+  can lose a few bits where a propagator is close to its pole, and the
+  diagram cancellation kappa; the median must stay below 4e-6.  Median and
+  maximum are printed.
 """
 import math
 
@@ -31,8 +33,11 @@ def fp64_tol(kappa):
     return np.maximum(FP64_TOL, 64 * U64 * kappa)
 
 
+MIXED_MEDIAN_TOL = 4e-6
+
+
 def mixed_tol(k, kappa):
-    return 4 * (2 * (k + 1) - 1) * U32 * np.maximum(kappa, 1.0)
+    return 32 * (2 * (k + 1) - 1) * U32 * np.maximum(kappa, 1.0)
 
 # (k, summed, omega, points compared with the oracle)
 CASES = [
@@ -74,6 +79,8 @@ def test_parity_vs_oracle(orc, k, summed, omega, npts, precision):
     tol = fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)
     bad = np.nonzero(rel > tol)[0]
     assert bad.size == 0, (bad[:5], rel[bad[:5]], kap[bad[:5]])
+    if precision == "mixed":
+        assert np.median(rel) <= MIXED_MEDIAN_TOL
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 127, 1000, 4099])
