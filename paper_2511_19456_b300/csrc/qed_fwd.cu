@@ -199,7 +199,7 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double vim() const { return (double)im - (double)cim; }
 };
 
-template <int K, bool SUMMED, typename Real, int TEAM>
+template <int K, bool SUMMED, typename Real, int TEAM, int ES>
 __global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256)
 qed_fwd_kernel(const KParams p) {
   constexpr int N = K + 1;
@@ -213,7 +213,13 @@ qed_fwd_kernel(const KParams p) {
   constexpr int NL = [] { int f = 1; for (int i = 2; i <= H; ++i) f *= i; return f; }();
   constexpr int NR = [] { int f = 1; for (int i = 2; i <= R; ++i) f *= i; return f; }();
   constexpr int BC = NR >= 2 ? 2 : 1;   // right leaves held in registers
-  constexpr int GA = NL % 2 == 0 ? 2 : 1; // left leaves per compensated step
+  constexpr int GA = NL % 3 == 0 ? 3 : (NL % 2 == 0 ? 2 : 1); // left leaves per compensated step
+  // Summed spin: ES threads share one photon-polarisation pattern and split
+  // its 4 electron-helicity pairs (ES = 1: all 4; 2: one incoming helicity
+  // each; 4: one pair each).
+  constexpr int NSI = ES >= 2 ? 1 : 2;
+  constexpr int NSO = ES >= 4 ? 1 : 2;
+  static_assert(!SUMMED || TEAM == (1 << N) * ES, "team = polarisation patterns x helicity split");
 
   extern __shared__ __align__(16) unsigned char smem[];
   const TeamLayout L = team_layout(K, (int)sizeof(Real), p.ncur);
@@ -276,7 +282,7 @@ qed_fwd_kernel(const KParams p) {
       team_sync<TEAM>();
     }
 
-    Acc<Real> acc[SUMMED ? 4 : 1];
+    Acc<Real> acc[SUMMED ? NSI * NSO : 1];
     for (int s = 0; s < p.n_sets; ++s) {
       const SetEntry se = p.sets[s];
       for (int t = 0; t < p.n_set_phases; ++t) {
@@ -286,43 +292,44 @@ qed_fwd_kernel(const KParams p) {
       }
       // ---- a6/a7: S2 joins of every diagram whose left photon set is S
       if constexpr (SUMMED) {
-        const unsigned c = (unsigned)lane;
-        const int vl = (int)pext_bits(c, se.mask, N) << 1;
-        const int vr = (int)pext_bits(c, ALL & ~se.mask, N) << 1;
+        const unsigned c = (unsigned)lane & ALL;
+        const int ep = lane >> N;
+        const int vl = ((int)pext_bits(c, se.mask, N) << 1) + (ES >= 2 ? (ep & 1) : 0);
+        const int vr = ((int)pext_bits(c, ALL & ~se.mask, N) << 1) + (ES >= 4 ? (ep >> 1) : 0);
 
         for (int b0 = 0; b0 < NR; b0 += BC) {
-          Real rw[BC][2][8];
+          Real rw[BC][NSO][8];
 #pragma unroll
           for (int bb = 0; bb < BC; ++bb)
 #pragma unroll
-            for (int so = 0; so < 2; ++so)
+            for (int so = 0; so < NSO; ++so)
               load_cur(s_cur, se.leaf_r + (b0 + bb) * NVR, NVR, vr + so, rw[bb][so]);
           for (int a0 = 0; a0 < NL; a0 += GA) {
-            Real lc[GA][2][8];
+            Real lc[GA][NSI][8];
 #pragma unroll
             for (int ga = 0; ga < GA; ++ga)
 #pragma unroll
-              for (int si = 0; si < 2; ++si)
+              for (int si = 0; si < NSI; ++si)
                 load_cur(s_cur, se.leaf_l + (a0 + ga) * NVL, NVL, vl + si, lc[ga][si]);
 #pragma unroll
-            for (int si = 0; si < 2; ++si)
+            for (int si = 0; si < NSI; ++si)
 #pragma unroll
-              for (int so = 0; so < 2; ++so) {
+              for (int so = 0; so < NSO; ++so) {
                 if constexpr (sizeof(Real) == 8) {
 #pragma unroll
                   for (int ga = 0; ga < GA; ++ga)
 #pragma unroll
                     for (int bb = 0; bb < BC; ++bb)
-                      dot_acc(rw[bb][so], lc[ga][si], acc[si * 2 + so].re, acc[si * 2 + so].im);
+                      dot_acc(rw[bb][so], lc[ga][si], acc[si * NSO + so].re, acc[si * NSO + so].im);
                 } else {
                   // the GA x BC diagrams of this state in one compensated step
                   float yr, yi;
-                  acc[si * 2 + so].start(yr, yi);
+                  acc[si * NSO + so].start(yr, yi);
 #pragma unroll
                   for (int ga = 0; ga < GA; ++ga)
 #pragma unroll
                     for (int bb = 0; bb < BC; ++bb) dot_acc(rw[bb][so], lc[ga][si], yr, yi);
-                  acc[si * 2 + so].commit(yr, yi);
+                  acc[si * NSO + so].commit(yr, yi);
                 }
               }
           }
@@ -353,13 +360,13 @@ qed_fwd_kernel(const KParams p) {
       if constexpr (sizeof(Real) == 8) {
         part = 0.0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) part = fma(acc[i].re, acc[i].re, fma(acc[i].im, acc[i].im, part));
+        for (int i = 0; i < NSI * NSO; ++i) part = fma(acc[i].re, acc[i].re, fma(acc[i].im, acc[i].im, part));
       } else {
         // squares of the compensated amplitudes, exact to ~2^-48 in
         // float-float; the sum over the team's states in FP64
         float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NSI * NSO; ++i) {
           add_square_ff(acc[i].re, acc[i].cre, hi, lo);
           add_square_ff(acc[i].im, acc[i].cim, hi, lo);
         }
@@ -377,30 +384,40 @@ qed_fwd_kernel(const KParams p) {
 }
 
 // ----------------------------------------------------------- dispatch
-template <int K, bool SUMMED>
+// Summed spin: one thread keeps all 4 helicity pairs of a polarisation
+// pattern (ES = 1); splitting them over more threads (ES = 2, 4) raises the
+// threads per point but halves the FMAs per shared-memory load of the join,
+// which measured slower for both precisions.  Fixed spin: a team of up to
+// one warp splits the diagrams.
+template <int K, bool SUMMED, bool MIXED>
+constexpr int es_of() { return 1; }
+
+template <int K, bool SUMMED, bool MIXED>
 constexpr int team_of() {
-  if constexpr (SUMMED) return 1 << (K + 1);
+  if constexpr (SUMMED) return (1 << (K + 1)) * es_of<K, SUMMED, MIXED>();
   else return K == 1 ? 2 : (K == 2 ? 4 : (K == 3 ? 8 : (K == 4 ? 16 : 32)));
 }
 
 using KernelFn = void (*)(const KParams);
-
-template <int K, bool SUMMED>
-KernelFn pick(bool mixed) {
-  constexpr int T = team_of<K, SUMMED>();
-  return mixed ? qed_fwd_kernel<K, SUMMED, float, T> : qed_fwd_kernel<K, SUMMED, double, T>;
-}
 
 struct KernelChoice {
   KernelFn fn;
   int team;
 };
 
+template <int K, bool SUMMED>
+KernelChoice pick(bool mixed) {
+  if (mixed) {
+    constexpr int T = team_of<K, SUMMED, true>();
+    return {qed_fwd_kernel<K, SUMMED, float, T, es_of<K, SUMMED, true>()>, T};
+  }
+  constexpr int T = team_of<K, SUMMED, false>();
+  return {qed_fwd_kernel<K, SUMMED, double, T, es_of<K, SUMMED, false>()>, T};
+}
+
 KernelChoice forward_kernel(int k, bool summed, bool mixed) {
-#define QED_CASE(KK)                                                                  \
-  case KK:                                                                            \
-    return summed ? KernelChoice{pick<KK, true>(mixed), team_of<KK, true>()}          \
-                  : KernelChoice{pick<KK, false>(mixed), team_of<KK, false>()};
+#define QED_CASE(KK) \
+  case KK: return summed ? pick<KK, true>(mixed) : pick<KK, false>(mixed);
   switch (k) {
     QED_CASE(1) QED_CASE(2) QED_CASE(3) QED_CASE(4) QED_CASE(5) QED_CASE(6) QED_CASE(7)
     default: return KernelChoice{nullptr, 0};
