@@ -37,6 +37,21 @@ FP32_LANES_PER_SM = 128
 # FP32 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz; FP64 the nominal B300 rate.
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 1.25
+# Version of the forward kernel (arithmetic, shared-memory layout, launch
+# shape); bumped with every change to it.  DRAM traffic recorded in
+# profiles/traffic.json is reported only for the version it was measured on.
+FWD_KERNEL_VERSION = "fwd-3"
+
+
+def recorded_traffic(workload: str, prec: str, n_points: int):
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(f"{workload}/{prec}")
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_version") != FWD_KERNEL_VERSION or rec.get("n_points") != n_points:
+        return None
+    return rec["bytes_per_launch"]
 
 
 def dist_env():
@@ -242,7 +257,10 @@ def main():
         peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
         res[prec] = {"value": pts, "ms_per_step": ms, "plan": plan, "info": info,
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                                  "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                                  "unit": "TFLOP/s", "frac": achieved / peak,
+                                  "traffic": recorded_traffic(args.workload, prec, n),
+                                  "peak_source": "derived from unit counts and the 2032 MHz clock"
+                                  if prec == "mixed" else "nominal B300 FP64 rate",
                                   "pipe": "FP32 FMA" if prec == "mixed" else "FP64 FMA",
                                   "flops_per_point": flops},
                      "clocks": cs.summary()}

@@ -1,0 +1,498 @@
+// Adjoint kernels: |M|^2 and d|M|^2 / d k_j for the outgoing photons' 3-momenta
+// (slots 3..k+2, energies on shell E_j = |k_j|; p, k_0 and p' held fixed).
+//
+// Reverse mode through the same node-reduced DAG as the forward kernels.
+// With f = sum_l |M_l|^2, df = 2 Re sum_l conj(M_l) dM_l.  Every complex
+// intermediate z gets an adjoint zbar such that sum_l conj(M_l) dM_l =
+// sum zbar . dz (bilinear, no conjugation); a linear step z = W x passes
+// xbar = W^T zbar and contributes zbar^T dW x for parameters inside W.
+//
+// Per point:
+//   1. forward pass (as the forward kernel) -> M_l, |M|^2;
+//   2. seeds Mbar_l = conj(M_l) in shared memory;
+//   3. for every photon set S: rebuild the set's currents (sub-currents are
+//      recomputed, not stored), transposed joins give the leaf adjoints
+//        Lbar_a = sum_b sum_l Mbar_l R'_b,   R'bar_b = sum_a sum_l Mbar_l L_a,
+//      then the set's instructions in reverse order pass adjoints to their
+//      inputs and accumulate the parameter terms;
+//   4. the kept inner levels in reverse order;
+//   5. parameter adjoints -> photon momenta:
+//        propagator of subset T (P = (Q/ + m)/D): with s_mu = ybar gamma^mu w
+//        and u = ybar . y summed over its uses,
+//          df/dQ^mu = 2 Re[eta_mu (s_mu - 2 Q^mu u) / D],
+//        Q_T = p + sum_{j in T} c_j k_j;
+//        vertex of photon j (eps/ = -gamma^i eps^i): with e_i = -wbar gamma^i x,
+//          df/deps^i = 2 Re e_i, chained through eps_pol(k_j);
+//        finally dE_j/dk_j = k_j / |k_j|.
+// Parameter accumulators are FP64 in shared memory (atomic adds); currents and
+// their adjoints are in the working precision.
+#include <cuda_runtime.h>
+
+#include "qed_team.cuh"
+
+namespace qed {
+
+namespace {
+
+template <typename Real>
+struct Cf {
+  Real re, im;
+};
+
+template <typename Real>
+__device__ __forceinline__ Cf<Real> cmul(Real ar, Real ai, Real br, Real bi) {
+  return {ar * br - ai * bi, ar * bi + ai * br};
+}
+
+// s_mu = sum_ab a_a gamma^mu_ab b_b (mu = 0..3, Dirac representation) and
+// u = sum_c a_c b_c, for complex 4-vectors a, b stored as 8 reals.
+template <typename Real>
+__device__ __forceinline__ void bilinears(const Real* a, const Real* b, Cf<Real> s[4], Cf<Real>& u) {
+  Cf<Real> ab[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ab[i][j] = cmul(a[2 * i], a[2 * i + 1], b[2 * j], b[2 * j + 1]);
+  // gamma^0 = diag(1, 1, -1, -1)
+  s[0] = {ab[0][0].re + ab[1][1].re - ab[2][2].re - ab[3][3].re,
+          ab[0][0].im + ab[1][1].im - ab[2][2].im - ab[3][3].im};
+  u = {ab[0][0].re + ab[1][1].re + ab[2][2].re + ab[3][3].re,
+       ab[0][0].im + ab[1][1].im + ab[2][2].im + ab[3][3].im};
+  // gamma^i = [[0, sigma^i], [-sigma^i, 0]]:  a_u sigma^i b_l - a_l sigma^i b_u
+  // x sigma^1 y = x0 y1 + x1 y0
+  s[1] = {ab[0][3].re + ab[1][2].re - ab[2][1].re - ab[3][0].re,
+          ab[0][3].im + ab[1][2].im - ab[2][1].im - ab[3][0].im};
+  // x sigma^2 y = i (x1 y0 - x0 y1)
+  {
+    const Real tr = (ab[1][2].re - ab[0][3].re) - (ab[3][0].re - ab[2][1].re);
+    const Real ti = (ab[1][2].im - ab[0][3].im) - (ab[3][0].im - ab[2][1].im);
+    s[2] = {-ti, tr};
+  }
+  // x sigma^3 y = x0 y0 - x1 y1
+  s[3] = {ab[0][2].re - ab[1][3].re - ab[2][0].re + ab[3][1].re,
+          ab[0][2].im - ab[1][3].im - ab[2][0].im + ab[3][1].im};
+}
+
+__device__ __forceinline__ void atomic_add_c(double* p, double re, double im) {
+  atomicAdd(p, re);
+  atomicAdd(p + 1, im);
+}
+
+template <typename Real>
+__device__ __forceinline__ void atomic_add_cur(Real* p, int nv, const Real x[8]) {
+  typedef typename C2<Real>::T T;
+  (void)sizeof(T);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) atomicAdd(p + i, x[i]);
+  (void)nv;
+}
+
+// One instruction output variant v (polarisation pol): given its adjoint ybar
+// and its input x, accumulate the parameter terms and return the input's
+// adjoint contribution in xbar (added).
+template <typename Real>
+__device__ __forceinline__ void backprop_one(const Instr& in, int pol, const Real x[8], const Real yb[8],
+                                             const Real* s_q, const Real* s_eps, double* s_acc_s,
+                                             double* s_acc_e, Real xbar[8]) {
+  const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
+  const Real ev[3] = {e3[0], e3[1], e3[2]};
+  Real w[8], wb[8], t[8];
+  Cf<Real> s[4], u;
+  if (in.side == 0) {
+    vertex_col(ev, x, w);                       // w = eps/ x
+    if (in.post) {
+      const Real* P = s_q + in.post * 5;
+      Real y[8];
+      prop_col(P, w, y);                        // y = P w
+      prop_row(P, yb, wb);                      // wbar = ybar P
+      bilinears(yb, w, s, u);                   // s_mu = ybar g^mu w
+      Cf<Real> u2, sd[4];
+      bilinears(yb, y, sd, u2);                 // u = ybar . y
+      double* A = s_acc_s + in.post * 10;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) atomic_add_c(A + 2 * mu, (double)s[mu].re, (double)s[mu].im);
+      atomic_add_c(A + 8, (double)u2.re, (double)u2.im);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) wb[i] = yb[i];
+    }
+    vertex_row(ev, wb, t);                      // xbar += wbar eps/
+    bilinears(wb, x, s, u);                     // e_i = -wbar g^i x
+  } else {
+    vertex_row(ev, x, w);                       // w = x eps/
+    if (in.post) {
+      const Real* P = s_q + in.post * 5;
+      Real y[8];
+      prop_row(P, w, y);                        // y = w P
+      prop_col(P, yb, wb);                      // wbar = P ybar
+      bilinears(w, yb, s, u);                   // s_mu = w g^mu ybar
+      Cf<Real> u2, sd[4];
+      bilinears(y, yb, sd, u2);                 // u = y . ybar
+      double* A = s_acc_s + in.post * 10;
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) atomic_add_c(A + 2 * mu, (double)s[mu].re, (double)s[mu].im);
+      atomic_add_c(A + 8, (double)u2.re, (double)u2.im);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) wb[i] = yb[i];
+    }
+    vertex_col(ev, wb, t);                      // xbar += eps/ wbar
+    bilinears(x, wb, s, u);                     // e_i = -x g^i wbar
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) xbar[i] += t[i];
+  double* E = s_acc_e + (in.photon * 2 + pol) * 6;
+#pragma unroll
+  for (int i = 1; i < 4; ++i) atomic_add_c(E + 2 * (i - 1), -(double)s[i].re, -(double)s[i].im);
+}
+
+// Reverse of one phase: every instruction passes its outputs' adjoints to its
+// input (atomic adds: siblings share inputs).  Summed spin: item vp = one
+// input variant and both photon polarisations.
+template <int TEAM, bool SUMMED, typename Real>
+__device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const KParams& p,
+                                               const Real* s_q, const Real* s_eps,
+                                               const Real* s_spin, const Real* s_cur, Real* s_adj,
+                                               double* s_acc_s, double* s_acc_e) {
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+    const int cnt = ph.cnt[slot];
+    if (cnt == 0) continue;
+    const int lg = SUMMED ? ph.level[slot] : 0;
+    const int total = cnt << lg;
+    for (int it = lane; it < total; it += TEAM) {
+      const int i = it >> lg;
+      const int vp = it & ((1 << lg) - 1);
+      const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
+      Real x[8], xb[8], yb[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
+      if constexpr (SUMMED) {
+        const int nv = 2 << in.level;
+        if (in.src < 0) load8(s_spin + (in.side * 2 + vp) * 8, x);
+        else load_cur(s_cur, in.src, nv >> 1, vp, x);
+        const int b = 1 + in.rank;
+        const int lo = vp & ((1 << b) - 1);
+        const int hi = (vp >> b) << (b + 1);
+#pragma unroll
+        for (int pol = 0; pol < 2; ++pol) {
+          load_cur(s_adj, in.dst, nv, hi | (pol << b) | lo, yb);
+          backprop_one(in, pol, x, yb, s_q, s_eps, s_acc_s, s_acc_e, xb);
+        }
+      } else {
+        const int pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
+        if (in.src < 0) load8(s_spin + (in.side * 2 + (in.side == 0 ? p.fixed_sin : p.fixed_sout)) * 8, x);
+        else load_cur(s_cur, in.src, 1, 0, x);
+        load_cur(s_adj, in.dst, 1, 0, yb);
+        backprop_one(in, pol, x, yb, s_q, s_eps, s_acc_s, s_acc_e, xb);
+      }
+      if (in.src >= 0) atomic_add_cur(s_adj + (size_t)(in.src + vp) * 8, 0, xb);
+    }
+  }
+}
+
+// pdep: scatter the low bits of v into the set bits of mask.
+__device__ __forceinline__ unsigned pdep_bits(unsigned v, unsigned mask, int n) {
+  unsigned r = 0;
+  int o = 0;
+  for (int j = 0; j < n; ++j)
+    if (mask & (1u << j)) { r |= ((v >> o) & 1u) << j; ++o; }
+  return r;
+}
+
+// d eps_pol / d k_a (a = x, y, z) for the real linear polarisations; zero on
+// the z axis, where the basis is fixed by convention.
+__device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) {
+  const double kx = k[1], ky = k[2], kz = k[3];
+  const double kt2 = kx * kx + ky * ky;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[a][i] = 0.0;
+  if (kt2 == 0.0) return;
+  const double kt = sqrt(kt2);
+  if (pbit) {
+    // eps_2 = (-ky, kx, 0) / kT
+    const double c = 1.0 / (kt2 * kt);
+    d[0][0] = kx * ky * c; d[0][1] = ky * ky * c;
+    d[1][0] = -kx * kx * c; d[1][1] = -kx * ky * c;
+    return;
+  }
+  // eps_1 = g (kx kz, ky kz, -kT^2), g = 1 / (K kT)
+  const double K2 = kt2 + kz * kz;
+  const double K = sqrt(K2);
+  const double g = 1.0 / (K * kt);
+  const double num[3] = {kx * kz, ky * kz, -kt2};
+  const double dg[3] = {-g * (kx / K2 + kx / kt2), -g * (ky / K2 + ky / kt2), -g * kz / K2};
+  const double dn[3][3] = {{kz, 0.0, -2.0 * kx}, {0.0, kz, -2.0 * ky}, {kx, ky, 0.0}};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[a][i] = g * dn[a][i] + num[i] * dg[a];
+}
+
+}  // namespace
+
+template <int K, bool SUMMED, typename Real, int TEAM>
+__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256)
+qed_adj_kernel(const KParams p) {
+  constexpr int N = K + 1;
+  constexpr int H = (N + 1) / 2;
+  constexpr int R = N - H;
+  constexpr int NSUB = 1 << N;
+  constexpr unsigned ALL = (1u << N) - 1;
+  constexpr int NVL = SUMMED ? (1 << (H + 1)) : 1;
+  constexpr int NVR = SUMMED ? (1 << (R + 1)) : 1;
+  constexpr int NL = [] { int f = 1; for (int i = 2; i <= H; ++i) f *= i; return f; }();
+  constexpr int NR = [] { int f = 1; for (int i = 2; i <= R; ++i) f *= i; return f; }();
+  static_assert(!SUMMED || TEAM == (1 << N), "one thread per polarisation pattern");
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const AdjLayout A = adj_layout(K, (int)sizeof(Real), p.ncur, SUMMED);
+  const TeamLayout& L = A.fwd;
+  const int lane = threadIdx.x & (TEAM - 1);
+  const int team = threadIdx.x / TEAM;
+  const int tpc = blockDim.x / TEAM;
+  unsigned char* base = smem + (size_t)team * A.bytes;
+  double* s_mom = reinterpret_cast<double*>(base + L.mom);
+  Real* s_q = reinterpret_cast<Real*>(base + L.q);
+  Real* s_eps = reinterpret_cast<Real*>(base + L.eps);
+  Real* s_spin = reinterpret_cast<Real*>(base + L.spin);
+  double* s_red = reinterpret_cast<double*>(base + L.red);
+  Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
+  Real* s_adj = reinterpret_cast<Real*>(base + A.adj);
+  Real* s_mbar = reinterpret_cast<Real*>(base + A.mbar);
+  double* s_acc_s = reinterpret_cast<double*>(base + A.acc_s);
+  double* s_acc_e = reinterpret_cast<double*>(base + A.acc_e);
+  double* s_kbar = reinterpret_cast<double*>(base + A.kbar);
+
+  for (long long pt0 = (long long)blockIdx.x * tpc; pt0 < p.n; pt0 += (long long)gridDim.x * tpc) {
+    const long long pt = pt0 + team;
+    const bool valid = pt < p.n;
+    const long long ptc = valid ? pt : p.n - 1;
+
+    // ---- 1. forward pass
+    point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin);
+    for (int ph = 0; ph < p.n_stored_phases; ++ph) {
+      run_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur);
+      team_sync<TEAM>();
+    }
+    Acc<Real> acc[SUMMED ? 4 : 1];
+    for (int s = 0; s < p.n_sets; ++s) {
+      const SetEntry se = p.sets[s];
+      for (int t = 0; t < p.n_set_phases; ++t) {
+        run_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + se.phase0 + t), lane, p, s_q, s_eps, s_spin,
+                                      s_cur);
+        team_sync<TEAM>();
+      }
+      join_set<K, SUMMED, Real, TEAM, 1>(se, lane, s_cur, acc);
+      team_sync<TEAM>();
+    }
+
+    // ---- 2. |M|^2 and the seeds conj(M)
+    double m2;
+    if constexpr (SUMMED) {
+      double part = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double re = acc[i].vre(), im = acc[i].vim();
+        part = fma(re, re, fma(im, im, part));
+        const int lam = (i >> 1) | ((i & 1) << 1) | (lane << 2);   // i = 2 si + so
+        s_mbar[2 * lam] = (Real)re;
+        s_mbar[2 * lam + 1] = (Real)(-im);
+      }
+      m2 = team_sum<TEAM>(part, s_red);
+    } else {
+      const double re = team_sum<TEAM>(acc[0].vre(), s_red);
+      const double im = team_sum<TEAM>(acc[0].vim(), s_red);
+      m2 = re * re + im * im;
+      if (lane == 0) { s_mbar[0] = (Real)re; s_mbar[1] = (Real)(-im); }
+    }
+    if (lane == 0 && valid && p.out) p.out[pt] = m2 * p.coupling;
+
+    // zero the adjoints of the kept currents and the accumulators
+    {
+      const int nst = p.ncur_stored * 8;
+      for (int i = lane; i < nst; i += TEAM) s_adj[i] = (Real)0;
+      for (int i = lane; i < NSUB * 10; i += TEAM) s_acc_s[i] = 0.0;
+      for (int i = lane; i < N * 12; i += TEAM) s_acc_e[i] = 0.0;
+      for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
+    }
+    team_sync<TEAM>();
+
+    // ---- 3. per photon set: rebuild, transposed joins, reverse phases
+    for (int s = 0; s < p.n_sets; ++s) {
+      const SetEntry se = p.sets[s];
+      for (int i = p.ncur_stored * 8 + lane; i < p.ncur * 8; i += TEAM) s_adj[i] = (Real)0;
+      for (int t = 0; t < p.n_set_phases; ++t) {
+        run_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + se.phase0 + t), lane, p, s_q, s_eps, s_spin,
+                                      s_cur);
+        team_sync<TEAM>();
+      }
+      const unsigned S = se.mask, SC = ALL & ~S;
+      if constexpr (SUMMED) {
+        // left leaves: item (a, vL), vL = si + 2 pS
+        for (int it = lane; it < NL * NVL + NR * NVR; it += TEAM) {
+          Real acc8[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc8[c] = (Real)0;
+          if (it < NL * NVL) {
+            const int a = it / NVL, vL = it - a * NVL;
+            const int si = vL & 1;
+            const unsigned cs = pdep_bits((unsigned)(vL >> 1), S, N);
+            for (int b = 0; b < NR; ++b)
+              for (int vR = 0; vR < NVR; ++vR) {
+                const int so = vR & 1;
+                const unsigned c = cs | pdep_bits((unsigned)(vR >> 1), SC, N);
+                const int lam = si | (so << 1) | (int)(c << 2);
+                const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
+                Real rw[8];
+                load_cur(s_cur, se.leaf_r + b * NVR, NVR, vR, rw);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  acc8[2 * q] += mr * rw[2 * q] - mi * rw[2 * q + 1];
+                  acc8[2 * q + 1] += mr * rw[2 * q + 1] + mi * rw[2 * q];
+                }
+              }
+            store_cur(s_adj, se.leaf_l + a * NVL, NVL, vL, acc8);
+          } else {
+            const int jt = it - NL * NVL;
+            const int b = jt / NVR, vR = jt - b * NVR;
+            const int so = vR & 1;
+            const unsigned cc = pdep_bits((unsigned)(vR >> 1), SC, N);
+            for (int a = 0; a < NL; ++a)
+              for (int vL = 0; vL < NVL; ++vL) {
+                const int si = vL & 1;
+                const unsigned c = cc | pdep_bits((unsigned)(vL >> 1), S, N);
+                const int lam = si | (so << 1) | (int)(c << 2);
+                const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
+                Real lc[8];
+                load_cur(s_cur, se.leaf_l + a * NVL, NVL, vL, lc);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  acc8[2 * q] += mr * lc[2 * q] - mi * lc[2 * q + 1];
+                  acc8[2 * q + 1] += mr * lc[2 * q + 1] + mi * lc[2 * q];
+                }
+              }
+            store_cur(s_adj, se.leaf_r + b * NVR, NVR, vR, acc8);
+          }
+        }
+      } else {
+        const Real mr = s_mbar[0], mi = s_mbar[1];
+        for (int it = lane; it < NL + NR; it += TEAM) {
+          Real acc8[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc8[c] = (Real)0;
+          const bool left = it < NL;
+          const int cnt = left ? NR : NL;
+          for (int o = 0; o < cnt; ++o) {
+            Real v8[8];
+            load_cur(s_cur, left ? se.leaf_r + o : se.leaf_l + o, 1, 0, v8);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              acc8[2 * q] += mr * v8[2 * q] - mi * v8[2 * q + 1];
+              acc8[2 * q + 1] += mr * v8[2 * q + 1] + mi * v8[2 * q];
+            }
+          }
+          store_cur(s_adj, left ? se.leaf_l + it : se.leaf_r + (it - NL), 1, 0, acc8);
+        }
+      }
+      team_sync<TEAM>();
+      for (int t = p.n_set_phases - 1; t >= 0; --t) {
+        backprop_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + se.phase0 + t), lane, p, s_q, s_eps, s_spin,
+                                           s_cur, s_adj, s_acc_s, s_acc_e);
+        team_sync<TEAM>();
+      }
+    }
+
+    // ---- 4. kept inner levels, deepest first
+    for (int ph = p.n_stored_phases - 1; ph >= 0; --ph) {
+      backprop_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur, s_adj,
+                                         s_acc_s, s_acc_e);
+      team_sync<TEAM>();
+    }
+
+    // ---- 5. parameters -> outgoing photon momenta (FP64)
+    for (int mask = lane; mask < NSUB; mask += TEAM) {
+      if (mask == 0 || mask == (int)ALL) continue;
+      double q0 = s_mom[0], q1 = s_mom[1], q2 = s_mom[2], q3 = s_mom[3];
+      for (int j = 0; j < N; ++j) {
+        if (!(mask & (1 << j))) continue;
+        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
+        if (j == 0) { q0 += kj[0]; q1 += kj[1]; q2 += kj[2]; q3 += kj[3]; }
+        else        { q0 -= kj[0]; q1 -= kj[1]; q2 -= kj[2]; q3 -= kj[3]; }
+      }
+      double D = __dmul_rn(q0, q0);
+      D = __dsub_rn(D, __dmul_rn(q1, q1));
+      D = __dsub_rn(D, __dmul_rn(q2, q2));
+      D = __dsub_rn(D, __dmul_rn(q3, q3));
+      D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
+      const double* Ac = s_acc_s + mask * 10;
+      const double Q[4] = {q0, q1, q2, q3};
+      double qb[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        const double eta = mu == 0 ? 1.0 : -1.0;
+        qb[mu] = 2.0 * eta * (Ac[2 * mu] - 2.0 * Q[mu] * Ac[8]) / D;   // real part
+      }
+      for (int j = 1; j < N; ++j)
+        if (mask & (1 << j))
+#pragma unroll
+          for (int mu = 0; mu < 4; ++mu) atomicAdd(s_kbar + 4 * j + mu, -qb[mu]);
+    }
+    for (int it = lane; it < 2 * N; it += TEAM) {
+      const int j = it >> 1, pb = it & 1;
+      if (j == 0) continue;
+      const double* E = s_acc_e + (j * 2 + pb) * 6;
+      double d[3][3];
+      dpol(s_mom + 4 * (j + 2), pb, d);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double g = 2.0 * (E[0] * d[a][0] + E[2] * d[a][1] + E[4] * d[a][2]);
+        atomicAdd(s_kbar + 4 * j + 1 + a, g);
+      }
+    }
+    team_sync<TEAM>();
+    for (int it = lane; it < 3 * K; it += TEAM) {
+      const int j = 1 + it / 3, a = it % 3;
+      const double* kj = s_mom + 4 * (j + 2);
+      const double kn = sqrt(kj[1] * kj[1] + kj[2] * kj[2] + kj[3] * kj[3]);
+      const double g = s_kbar[4 * j + 1 + a] + s_kbar[4 * j] * kj[1 + a] / kn;
+      if (valid) p.grad[(pt * K + (j - 1)) * 3 + a] = g * p.coupling;
+    }
+    team_sync<TEAM>();
+  }
+}
+
+// ----------------------------------------------------------- dispatch
+using KernelFn = void (*)(const KParams);
+
+struct KernelChoice {
+  KernelFn fn;
+  int team;
+};
+
+template <int K, bool SUMMED>
+constexpr int adj_team() {
+  if constexpr (SUMMED) return 1 << (K + 1);
+  else return K == 1 ? 2 : (K == 2 ? 4 : (K == 3 ? 8 : (K == 4 ? 16 : 32)));
+}
+
+template <int K, bool SUMMED>
+KernelChoice pick_adj(bool mixed) {
+  constexpr int T = adj_team<K, SUMMED>();
+  if (mixed) return {qed_adj_kernel<K, SUMMED, float, T>, T};
+  return {qed_adj_kernel<K, SUMMED, double, T>, T};
+}
+
+KernelChoice adjoint_kernel(int k, bool summed, bool mixed) {
+#define QED_CASE(KK) \
+  case KK: return summed ? pick_adj<KK, true>(mixed) : pick_adj<KK, false>(mixed);
+  switch (k) {
+    QED_CASE(1) QED_CASE(2) QED_CASE(3) QED_CASE(4) QED_CASE(5) QED_CASE(6) QED_CASE(7)
+    default: return KernelChoice{nullptr, 0};
+  }
+#undef QED_CASE
+}
+
+}  // namespace qed

@@ -20,6 +20,7 @@ struct KernelChoice {
   int team;
 };
 KernelChoice forward_kernel(int k, bool summed, bool mixed);
+KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
 }  // namespace qed
@@ -40,6 +41,15 @@ struct qed_plan_s {
   size_t smem = 0;
   int team_bytes = 0;
   int fixed_sin = 0, fixed_sout = 0, fixed_pol[8] = {0};
+  // adjoint: its own schedule (fewer kept levels where shared memory is short)
+  Schedule sc_adj;
+  Instr* d_instr_adj = nullptr;
+  Phase* d_phases_adj = nullptr;
+  SetEntry* d_sets_adj = nullptr;
+  KernelChoice kc_adj{nullptr, 0};
+  int block_adj = 0, grid_adj = 0;
+  size_t smem_adj = 0;
+  bool has_adj = false;
   int device = 0;
   // staging for qed_eval_host
   double* d_stage = nullptr;
@@ -75,6 +85,9 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_instr);
   cudaFree(p->d_phases);
   cudaFree(p->d_sets);
+  cudaFree(p->d_instr_adj);
+  cudaFree(p->d_phases_adj);
+  cudaFree(p->d_sets_adj);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
@@ -98,6 +111,7 @@ KParams make_params(const qed_plan_s* P, const double* mom, long long n, double*
   kp.n_set_phases = P->sc.n_set_phases;
   kp.n_sets = (int)P->sc.sets.size();
   kp.ncur = P->sc.stored_currents + P->sc.local_currents;
+  kp.ncur_stored = P->sc.stored_currents;
   kp.team_bytes = P->team_bytes;
   kp.mass = P->mass;
   kp.coupling = std::pow(P->charge, 2.0 * (P->k + 1));
@@ -115,6 +129,50 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
   if (e != cudaSuccess) return e;
   if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
+}
+
+// The adjoint keeps the forward currents and their adjoints in shared
+// memory: take the deepest kept levels (ls, rs) whose team fits; if none
+// fits, qed_eval_grad reports QED_EUNSUPPORTED for this plan.
+qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
+  const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
+  P->kc_adj = adjoint_kernel(k, P->summed, mixed);
+  if (!P->kc_adj.fn) return QED_OK;
+  const int team = P->kc_adj.team;
+  const int block = team > 32 ? team : 32;
+  for (int lev = std::max(h - 1, r - 1); lev >= 0; --lev) {
+    const int ls = std::min(lev, h - 1), rs = std::min(lev, r - 1);
+    Schedule sc;
+    try {
+      sc = build_schedule(k, P->summed, ls, rs);
+    } catch (const std::bad_alloc&) {
+      return QED_ENOMEM;
+    } catch (...) {
+      return QED_EUNSUPPORTED;
+    }
+    const int ncur = sc.stored_currents + sc.local_currents;
+    AdjLayout A = adj_layout(k, mixed ? 4 : 8, ncur, P->summed);
+    const size_t smem = (size_t)(block / team) * A.bytes;
+    if (smem > (size_t)dev_smem) continue;
+    cudaError_t e = upload(&P->d_instr_adj, sc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases_adj, sc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets_adj, sc.sets);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)P->kc_adj.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc_adj.fn, block, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return QED_OK;
+    P->sc_adj = std::move(sc);
+    P->block_adj = block;
+    P->smem_adj = smem;
+    P->grid_adj = per_sm * sms;
+    P->has_adj = true;
+    return QED_OK;
+  }
+  return QED_OK;
 }
 
 qed_status launch_eval(const qed_plan_s* P, const double* d_mom, long long n, double* d_out,
@@ -235,6 +293,8 @@ qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
                                                       P->smem);
   if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
   P->grid = per_sm * sms;
+  qed_status as = setup_adjoint(P, mixed, dev_smem, sms);
+  if (as != QED_OK) { free_plan(P); return as; }
   *out = P;
   return QED_OK;
 }
@@ -276,10 +336,25 @@ qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, dou
                          double* d_grad, void* stream) {
   if (!P || n < 0) return QED_EINVAL;
   if (n == 0) return QED_OK;
-  if (!d_momenta || !d_grad) return QED_EINVAL;
-  (void)d_out_m2;
-  (void)stream;
-  return QED_EUNSUPPORTED;
+  if (!d_momenta || !d_grad || !aligned8(d_momenta) || !aligned8(d_grad) ||
+      (d_out_m2 && !aligned8(d_out_m2)))
+    return QED_EINVAL;
+  if (!P->has_adj) return QED_EUNSUPPORTED;
+  KParams kp = make_params(P, d_momenta, n, d_out_m2);
+  kp.grad = d_grad;
+  kp.instr = P->d_instr_adj;
+  kp.phases = P->d_phases_adj;
+  kp.sets = P->d_sets_adj;
+  kp.n_stored_phases = P->sc_adj.n_stored_phases;
+  kp.n_set_phases = P->sc_adj.n_set_phases;
+  kp.n_sets = (int)P->sc_adj.sets.size();
+  kp.ncur = P->sc_adj.stored_currents + P->sc_adj.local_currents;
+  kp.ncur_stored = P->sc_adj.stored_currents;
+  const int tpc = P->block_adj / P->kc_adj.team;
+  const long long need = (n + tpc - 1) / tpc;
+  const int grid = (int)std::min<long long>(need, P->grid_adj);
+  return cuda_status(launch_forward(P->kc_adj.fn, grid, P->block_adj, P->smem_adj,
+                                    (cudaStream_t)stream, kp));
 }
 
 qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, double* h_out_m2,

@@ -1,0 +1,314 @@
+// Team-level building blocks shared by the forward and adjoint kernels: team
+// synchronisation and reductions, shared-memory current access, and the
+// execution of one phase of the linear schedule (V with optional S1 per spin
+// variant).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qed_device.cuh"
+
+namespace qed {
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TEAM <= 32) __syncwarp();
+  else __syncthreads();
+}
+
+template <int TEAM>
+__device__ __forceinline__ double team_sum(double v, double* red) {
+#pragma unroll
+  for (int off = (TEAM < 32 ? TEAM : 32) / 2; off > 0; off >>= 1)
+    v += __shfl_xor_sync(0xffffffffu, v, off);
+  if constexpr (TEAM > 32) {
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < TEAM / 32; ++i) s += red[i];
+    v = s;
+    __syncthreads();
+  }
+  return v;
+}
+
+// Currents live in shared memory component-major: a node whose current has
+// nv spin variants occupies 4*nv complex slots starting at 4*base, component
+// c of variant v at slot 4*base + c*nv + v.  Threads that work on
+// neighbouring variants then touch neighbouring 8- (FP32) or 16-byte (FP64)
+// words, free of bank conflicts.
+template <typename Real> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+// contiguous layout: variant v of node base at 8*(base+v) reals
+__device__ __forceinline__ void load_cur(const float* cur, int base, int nv, int v, float x[8]) {
+  const float4* q = reinterpret_cast<const float4*>(cur + (size_t)(base + v) * 8);
+  const float4 a = q[0], b = q[1];
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void store_cur(float* cur, int base, int nv, int v, const float x[8]) {
+  float4* q = reinterpret_cast<float4*>(cur + (size_t)(base + v) * 8);
+  q[0] = make_float4(x[0], x[1], x[2], x[3]);
+  q[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+__device__ __forceinline__ void load_cur(const double* cur, int base, int nv, int v, double x[8]) {
+  const double2* q = reinterpret_cast<const double2*>(cur + (size_t)(base + v) * 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { const double2 a = q[i]; x[2 * i] = a.x; x[2 * i + 1] = a.y; }
+}
+__device__ __forceinline__ void store_cur(double* cur, int base, int nv, int v, const double x[8]) {
+  double2* q = reinterpret_cast<double2*>(cur + (size_t)(base + v) * 8);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = make_double2(x[2 * i], x[2 * i + 1]);
+}
+// External spinors: 8 contiguous reals.
+template <typename Real>
+__device__ __forceinline__ void load8(const Real* p, Real x[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = p[i];
+}
+template <typename Real>
+__device__ __forceinline__ void store8(Real* p, const Real x[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = x[i];
+}
+
+__device__ __forceinline__ Instr ld_instr(const Instr* p) {
+  int4 v = __ldg(reinterpret_cast<const int4*>(p));
+  Instr in;
+  static_assert(sizeof(Instr) == sizeof(int4), "Instr size");
+  memcpy(&in, &v, sizeof(Instr));
+  return in;
+}
+
+// Vertex (+ propagation) of one input current x for photon polarisation pol,
+// stored as variant v of the instruction's node.
+template <typename Real>
+__device__ __forceinline__ void vertex_store(const Instr& in, const Real x[8], int pol, int v, int nv,
+                                             const Real* s_q, const Real* s_eps, Real* s_cur) {
+  const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
+  const Real ev[3] = {e3[0], e3[1], e3[2]};
+  Real y[8], z[8];
+  if (in.side == 0) vertex_col(ev, x, y); else vertex_row(ev, x, y);
+  if (in.post) {
+    const Real* P = s_q + in.post * 5;
+    if (in.side == 0) prop_col(P, y, z); else prop_row(P, y, z);
+    store_cur(s_cur, in.dst, nv, v, z);
+  } else {
+    store_cur(s_cur, in.dst, nv, v, y);
+  }
+}
+
+template <bool SUMMED, typename Real>
+__device__ __forceinline__ void apply_instr(const Instr& in, int v, const KParams& p,
+                                            const Real* s_q, const Real* s_eps,
+                                            const Real* s_spin, Real* s_cur) {
+  int pol, vp;
+  if constexpr (SUMMED) {
+    const int b = 1 + in.rank;
+    pol = (v >> b) & 1;
+    vp = (v & ((1 << b) - 1)) | ((v >> (b + 1)) << b);
+  } else {
+    pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
+    vp = 0;
+  }
+  Real x[8];
+  if (in.src < 0) {
+    const int e = SUMMED ? vp : (in.side == 0 ? p.fixed_sin : p.fixed_sout);
+    load8(s_spin + (in.side * 2 + e) * 8, x);
+  } else {
+    load_cur(s_cur, in.src, 0, vp, x);
+  }
+  vertex_store(in, x, pol, v, 0, s_q, s_eps, s_cur);
+}
+
+template <int TEAM, bool SUMMED, typename Real>
+__device__ __forceinline__ void run_phase(const Phase& ph, int lane, const KParams& p,
+                                          const Real* s_q, const Real* s_eps,
+                                          const Real* s_spin, Real* s_cur) {
+#pragma unroll
+  for (int slot = 0; slot < 2; ++slot) {
+    const int cnt = ph.cnt[slot];
+    if (cnt == 0) continue;
+    const int lg = SUMMED ? ph.level[slot] + 1 : 0;
+    const int total = cnt << lg;
+    for (int it = lane; it < total; it += TEAM) {
+      const int i = it >> lg;
+      const int v = it & ((1 << lg) - 1);
+      const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
+      apply_instr<SUMMED, Real>(in, v, p, s_q, s_eps, s_spin, s_cur);
+    }
+  }
+}
+
+__device__ __forceinline__ Phase ld_phase(const Phase* p) {
+  Phase ph;
+  const int* s = reinterpret_cast<const int*>(p);
+  int* d = reinterpret_cast<int*>(&ph);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = __ldg(s + i);
+  return ph;
+}
+
+// Per-state accumulator of the diagram sum.
+template <typename Real> struct Acc;
+template <> struct Acc<double> {
+  double re = 0.0, im = 0.0;
+  __device__ __forceinline__ void add(double r, double i) { re += r; im += i; }
+  __device__ __forceinline__ double vre() const { return re; }
+  __device__ __forceinline__ double vim() const { return im; }
+};
+// Kahan-compensated: the represented value is (re - cre, im - cim).  A group of
+// diagrams is accumulated by an FMA chain that starts from -c (the first
+// step of a Kahan update), then committed with the remaining two steps.
+template <> struct Acc<float> {
+  float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
+  __device__ __forceinline__ void start(float& yr, float& yi) const { yr = -cre; yi = -cim; }
+  __device__ __forceinline__ void commit(float yr, float yi) {
+    const float tr = __fadd_rn(re, yr), ti = __fadd_rn(im, yi);
+    cre = __fsub_rn(__fsub_rn(tr, re), yr);
+    cim = __fsub_rn(__fsub_rn(ti, im), yi);
+    re = tr;
+    im = ti;
+  }
+  __device__ __forceinline__ void add(float r, float i) {
+    float yr, yi;
+    start(yr, yi);
+    commit(__fadd_rn(yr, r), __fadd_rn(yi, i));
+  }
+  __device__ __forceinline__ double vre() const { return (double)re - (double)cre; }
+  __device__ __forceinline__ double vim() const { return (double)im - (double)cim; }
+};
+
+// Per point: momenta into shared memory, the propagator table (a3) and the
+// external states (a2).
+template <int K, typename Real, int TEAM>
+__device__ __forceinline__ void point_setup(const KParams& p, int lane, long long ptc, double* s_mom,
+                                          Real* s_q, Real* s_eps, Real* s_spin) {
+  constexpr int N = K + 1;
+  constexpr int NS = K + 3;
+  constexpr int NSUB = 1 << N;
+  constexpr unsigned ALL = (1u << N) - 1;
+  // ---- a1: load the point
+  for (int i = lane; i < NS * 4; i += TEAM) s_mom[i] = __ldg(p.mom + ptc * (NS * 4) + i);
+  team_sync<TEAM>();
+
+  // ---- a3: propagator entries of every photon subset, one subset per
+  // thread (momenta and denominators in FP64)
+  for (int mask = lane; mask < NSUB; mask += TEAM) {
+    Real* d = s_q + mask * 5;
+    Real P[5];
+    if (mask == 0 || mask == (int)ALL) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) P[c] = (Real)0;
+    } else {
+      make_prop<Real>(s_mom, N, (unsigned)mask, p.mass, P);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) d[c] = P[c];
+  }
+  // ---- a2: external states u(p, +-), ubar(p', +-), eps_j(pol 1, 2) in
+  // the working precision
+  for (int it = lane; it < 4 + 2 * N; it += TEAM) {
+    if (it < 4) {
+      const int side = it >> 1, e = it & 1;
+      Real s[8];
+      make_spinor<Real>(s_mom + (side ? 8 : 0), e, p.mass, side == 1, s);
+      store8(s_spin + (side * 2 + e) * 8, s);
+    } else {
+      const int j = (it - 4) >> 1, pb = (it - 4) & 1;
+      Real e[3];
+      make_pol<Real>(s_mom + 4 * (j == 0 ? 1 : j + 2), pb, e);
+      Real* d = s_eps + (j * 2 + pb) * 4;
+      d[0] = e[0]; d[1] = e[1]; d[2] = e[2]; d[3] = (Real)0;
+    }
+  }
+  team_sync<TEAM>();
+
+}
+
+// The S2 joins of every diagram whose left photon set is se.mask (a6), summed
+// per spin state into acc (a7).
+template <int K, bool SUMMED, typename Real, int TEAM, int ES>
+__device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Real* s_cur,
+                                       Acc<Real>* acc) {
+  constexpr int N = K + 1;
+  constexpr int H = (N + 1) / 2;
+  constexpr int R = N - H;
+  constexpr int NS = K + 3;
+  constexpr int NSUB = 1 << N;
+  constexpr unsigned ALL = (1u << N) - 1;
+  constexpr int NVL = SUMMED ? (1 << (H + 1)) : 1;
+  constexpr int NVR = SUMMED ? (1 << (R + 1)) : 1;
+  constexpr int NL = [] { int f = 1; for (int i = 2; i <= H; ++i) f *= i; return f; }();
+  constexpr int NR = [] { int f = 1; for (int i = 2; i <= R; ++i) f *= i; return f; }();
+  constexpr int BC = NR >= 2 ? 2 : 1;   // right leaves held in registers
+  constexpr int GA = NL % 3 == 0 ? 3 : (NL % 2 == 0 ? 2 : 1); // left leaves per compensated step
+  constexpr int NSI = ES >= 2 ? 1 : 2;
+  constexpr int NSO = ES >= 4 ? 1 : 2;
+    if constexpr (SUMMED) {
+      const unsigned c = (unsigned)lane & ALL;
+      const int ep = lane >> N;
+      const int vl = ((int)pext_bits(c, se.mask, N) << 1) + (ES >= 2 ? (ep & 1) : 0);
+      const int vr = ((int)pext_bits(c, ALL & ~se.mask, N) << 1) + (ES >= 4 ? (ep >> 1) : 0);
+
+      for (int b0 = 0; b0 < NR; b0 += BC) {
+        Real rw[BC][NSO][8];
+#pragma unroll
+        for (int bb = 0; bb < BC; ++bb)
+#pragma unroll
+          for (int so = 0; so < NSO; ++so)
+            load_cur(s_cur, se.leaf_r + (b0 + bb) * NVR, NVR, vr + so, rw[bb][so]);
+        for (int a0 = 0; a0 < NL; a0 += GA) {
+          Real lc[GA][NSI][8];
+#pragma unroll
+          for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+            for (int si = 0; si < NSI; ++si)
+              load_cur(s_cur, se.leaf_l + (a0 + ga) * NVL, NVL, vl + si, lc[ga][si]);
+#pragma unroll
+          for (int si = 0; si < NSI; ++si)
+#pragma unroll
+            for (int so = 0; so < NSO; ++so) {
+              if constexpr (sizeof(Real) == 8) {
+#pragma unroll
+                for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+                  for (int bb = 0; bb < BC; ++bb)
+                    dot_acc(rw[bb][so], lc[ga][si], acc[si * NSO + so].re, acc[si * NSO + so].im);
+              } else {
+                // the GA x BC diagrams of this state in one compensated step
+                float yr, yi;
+                acc[si * NSO + so].start(yr, yi);
+#pragma unroll
+                for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+                  for (int bb = 0; bb < BC; ++bb) dot_acc(rw[bb][so], lc[ga][si], yr, yi);
+                acc[si * NSO + so].commit(yr, yi);
+              }
+            }
+        }
+      }
+    } else {
+      for (int q = lane; q < NL * NR; q += TEAM) {
+        const int a = q / NR, b = q - a * NR;
+        Real lc[8], rw[8];
+        load_cur(s_cur, se.leaf_l + a, 1, 0, lc);
+        load_cur(s_cur, se.leaf_r + b, 1, 0, rw);
+        if constexpr (sizeof(Real) == 8) {
+          dot_acc(rw, lc, acc[0].re, acc[0].im);
+        } else {
+          float yr, yi;
+          acc[0].start(yr, yi);
+          dot_acc(rw, lc, yr, yi);
+          acc[0].commit(yr, yi);
+        }
+      }
+    }
+}
+
+}  // namespace qed

@@ -35,15 +35,40 @@ QED_HD TeamLayout team_layout(int k, int real_size, int ncur) {
   return L;
 }
 
+// Extra shared memory of the adjoint kernel after the forward team layout:
+// adjoints of every current, the amplitude seeds conj(M), and FP64
+// accumulators of the propagator (4 Dirac components + 1, complex) and
+// polarisation (3 components, complex) parameters and of the photon momenta.
+struct AdjLayout {
+  TeamLayout fwd;
+  int adj, mbar, acc_s, acc_e, kbar, bytes;
+};
+
+QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed) {
+  const int n = k + 1;
+  AdjLayout A;
+  A.fwd = team_layout(k, real_size, ncur);
+  int off = A.fwd.bytes;
+  A.adj = off;   off = align16(off + ncur * 8 * real_size);
+  A.mbar = off;  off = align16(off + (summed ? (1 << (n + 2)) : 1) * 2 * real_size);
+  A.acc_s = off; off = align16(off + (1 << n) * 10 * 8);
+  A.acc_e = off; off = align16(off + n * 2 * 6 * 8);
+  A.kbar = off;  off = align16(off + n * 4 * 8);
+  A.bytes = off;
+  return A;
+}
+
 struct KParams {
   const double* mom;
   double* out;
+  double* grad;      // adjoint kernel: d|M|^2/dk_j [N][k][3] (may be null otherwise)
   long long n;
   const Instr* instr;
   const Phase* phases;
   const SetEntry* sets;
   int n_stored_phases, n_set_phases, n_sets;
   int ncur;          // stored + local currents
+  int ncur_stored;   // currents kept for the whole point
   int team_bytes;
   double mass;
   double coupling;   // e^(2n)

@@ -1,0 +1,101 @@
+"""GPU adjoint: d|M|^2/dk_j of the outgoing photons against the oracle's
+dual-number gradient and against central differences of the GPU forward
+pass; plus the torch.autograd.Function.
+
+Tolerance (FP64): per point, max_j,a |g - g_ref| <= 1e-10 * max|g_ref|, or
+the kappa-scaled rounding bound 64 u64 kappa when that is larger.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_19456_b300 import Plan, phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+def fixed_hel(k):
+    return [1, 1, 1] + [1] * k if k == 6 else [1, 2, -1] + [1 + (j % 2) for j in range(k)]
+
+
+def gpu_grad(plan, mom):
+    d = torch.from_numpy(mom).cuda()
+    out, g = plan.eval_grad(d)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), g.cpu().numpy()
+
+
+CASES = [(1, True, 64), (2, True, 64), (3, True, 32), (4, True, 16), (5, True, 4),
+         (1, False, 64), (2, False, 64), (3, False, 64), (4, False, 32), (5, False, 16), (6, False, 256)]
+
+
+@pytest.mark.parametrize("k,summed,npts", CASES)
+def test_adjoint_vs_oracle_gradient(orc, k, summed, npts):
+    mom = ps.points(k, npts, 1.0 + k, seed=500 + k)
+    hel = None if summed else fixed_hel(k)
+    mask = orc.all_summed(k) if summed else 0
+    plan = Plan(k, summed=summed, hel=hel)
+    m2, g = gpu_grad(plan, mom)
+    ref_m2, ref_g = orc.grad(mom, sum_mask=mask, hel=hel)
+    _, kap = orc.m2(mom, sum_mask=mask, hel=hel, kappa=True)
+    assert np.allclose(m2, ref_m2, rtol=1e-12)
+    scale = np.abs(ref_g).max(axis=(1, 2))
+    err = np.abs(g - ref_g).max(axis=(1, 2)) / scale
+    tol = np.maximum(1e-10, 64 * U64 * kap)
+    print(f"\nk={k} summed={summed}: grad max rel err {err.max():.3e} median {np.median(err):.3e}")
+    assert np.all(err <= tol), (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("k,summed", [(4, True), (6, False)])
+def test_adjoint_vs_central_differences(k, summed):
+    mom = ps.points(k, 8, 1.0 + k, seed=600 + k)
+    plan = Plan(k, summed=summed, hel=None if summed else fixed_hel(k))
+    _, g = gpu_grad(plan, mom)
+    h = 1e-6
+    for j in range(k):
+        for a in range(3):
+            up, dn = mom.copy(), mom.copy()
+            up[:, 3 + j, 1 + a] += h
+            dn[:, 3 + j, 1 + a] -= h
+            for x in (up, dn):
+                x[:, 3 + j, 0] = np.linalg.norm(x[:, 3 + j, 1:], axis=1)
+            fu = plan.eval(torch.from_numpy(up).cuda()).cpu().numpy()
+            fd = plan.eval(torch.from_numpy(dn).cuda()).cpu().numpy()
+            fdg = (fu - fd) / (2 * h)
+            scale = np.abs(g).max(axis=(1, 2))
+            assert np.all(np.abs(fdg - g[:, j, a]) <= 1e-6 * scale + 5e-9 * np.abs(fu)), (j, a)
+
+
+def test_mixed_adjoint_close_to_fp64(orc):
+    k = 4
+    mom = ps.points(k, 16, 4.0, seed=610)
+    _, g64 = gpu_grad(Plan(k), mom)
+    _, g32 = gpu_grad(Plan(k, precision="mixed"), mom)
+    scale = np.abs(g64).max(axis=(1, 2))
+    err = np.abs(g32 - g64).max(axis=(1, 2)) / scale
+    print(f"\nmixed adjoint k=4: max rel err {err.max():.3e}")
+    assert err.max() < 1e-3
+
+
+def test_autograd_function():
+    from paper_2511_19456_b300.autograd import m2
+    k = 3
+    mom = torch.from_numpy(ps.points(k, 32, 3.0, seed=620)).cuda().requires_grad_(True)
+    plan = Plan(k)
+    out = m2(mom, plan)
+    w = torch.linspace(0.5, 1.5, 32, device="cuda", dtype=torch.float64)
+    (out * w).sum().backward()
+    _, g = plan.eval_grad(mom.detach())
+    expect = torch.zeros_like(mom)
+    expect[:, 3:, 1:] = w[:, None, None] * g
+    assert torch.allclose(mom.grad, expect, rtol=1e-13, atol=0)
+    assert torch.all(mom.grad[:, :3] == 0) and torch.all(mom.grad[:, :, 0] == 0)
+
+
+def test_grad_empty_and_errors():
+    plan = Plan(2)
+    d = torch.empty((0, 5, 4), dtype=torch.float64, device="cuda")
+    out, g = plan.eval_grad(d)
+    assert out.numel() == 0 and g.numel() == 0
