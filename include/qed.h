@@ -142,6 +142,36 @@ qed_status qed_eval_host(qed_plan_t plan, const double* h_momenta, long long n,
 
 void qed_plan_destroy(qed_plan_t plan);
 
+/* Batched evaluation of n_req requests of different k in ONE persistent
+ * launch (spin-summed plans, k <= 5, all of the same precision).  The host
+ * cuts request r's n_points[r] points into work items of about equal
+ * arithmetic, most expensive k first; persistent CTAs take items from a
+ * device counter, which never makes one CTA wait for another.  The counter
+ * reset and the launch are captured once in a CUDA graph.  The batch keeps
+ * the plans (they must outlive it), allocates its item list, request table
+ * and counter, and is not safe for concurrent use from two streams.
+ * Errors: QED_EINVAL (NULL, n < 0, mixed precisions), QED_EUNSUPPORTED
+ * (fixed spin, k > 5), QED_ENOMEM, QED_ECUDA. */
+qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long* n_points,
+                            qed_batch_t* out);
+
+/* Evaluates every request: d_momenta[r] -> d_out[r] (device pointers, sizes
+ * as given at creation).  Copies the request table (pointers) and replays the
+ * graph on `stream`; asynchronous. */
+qed_status qed_batch_eval(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
+                          void* stream);
+
+/* Autotuner: times block sizes {64, 128, 256} x item sizes {1e8 .. 6.4e9
+ * FLOPs} on the given buffers, keeps the fastest, rebuilds the graph and
+ * returns its time per evaluation in *best_ms (may be NULL).  Synchronous. */
+qed_status qed_batch_tune(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
+                          void* stream, double* best_ms);
+
+/* Current launch shape of a batch. */
+qed_status qed_batch_info(qed_batch_t batch, int* block, double* work_target, long long* n_items);
+
+void qed_batch_destroy(qed_batch_t batch);
+
 qed_status qed_dag_counts(int k, qed_dag_counts_t* out);
 
 const char* qed_status_string(qed_status status);

@@ -72,6 +72,14 @@ SIGNATURES = [
     ("qed_dag_counts", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(DagCounts)]),
     ("qed_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("qed_measure_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    ("qed_batch_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ll),
+                                        ctypes.POINTER(_vp)]),
+    ("qed_batch_eval", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    ("qed_batch_tune", ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    ("qed_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(_ll)]),
+    ("qed_batch_destroy", None, [_vp]),
     ("qed_schedule_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ScheduleDesc), _vp, _vp, _vp]),
 ]

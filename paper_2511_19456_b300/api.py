@@ -167,3 +167,67 @@ def measure_fma_peak(precision: str = "fp64", stream=None) -> float:
     check(_lib.lib().qed_measure_fma_peak(_PREC[precision], ctypes.byref(v), _stream_handle(stream)),
           "qed_measure_fma_peak")
     return v.value
+
+
+class Batch:
+    """Requests of different k evaluated in one persistent launch (CUDA graph).
+
+    plans: Plan objects (spin-summed, k <= 5, one precision); n_points: the
+    point count of each request.  The batch keeps references to the plans.
+    """
+
+    def __init__(self, plans, n_points):
+        self.plans = list(plans)
+        self.n_points = [int(n) for n in n_points]
+        nreq = len(self.plans)
+        ph = (ctypes.c_void_p * nreq)(*[p._h.value for p in self.plans])
+        nn = (ctypes.c_longlong * nreq)(*self.n_points)
+        h = ctypes.c_void_p()
+        check(_lib.lib().qed_batch_create(ph, nreq, nn, ctypes.byref(h)), "qed_batch_create")
+        self._h = h
+
+    def _ptrs(self, momenta, outs):
+        if len(momenta) != len(self.plans) or len(outs) != len(self.plans):
+            raise ValueError("one momenta tensor and one output per request")
+        for p, m, o, n in zip(self.plans, momenta, outs, self.n_points):
+            p._check_momenta(m, device=True)
+            if m.shape[0] != n or o.numel() != n:
+                raise ValueError("request sizes differ from the batch's")
+        nreq = len(self.plans)
+        return ((ctypes.c_void_p * nreq)(*[m.data_ptr() for m in momenta]),
+                (ctypes.c_void_p * nreq)(*[o.data_ptr() for o in outs]))
+
+    def outputs(self, device="cuda"):
+        torch = _torch()
+        return [torch.empty(n, dtype=torch.float64, device=device) for n in self.n_points]
+
+    def eval(self, momenta, outs=None, stream=None):
+        outs = self.outputs() if outs is None else outs
+        pm, po = self._ptrs(momenta, outs)
+        check(_lib.lib().qed_batch_eval(self._h, pm, po, _stream_handle(stream)), "qed_batch_eval")
+        return outs
+
+    def tune(self, momenta, outs=None, stream=None) -> float:
+        outs = self.outputs() if outs is None else outs
+        pm, po = self._ptrs(momenta, outs)
+        ms = ctypes.c_double()
+        check(_lib.lib().qed_batch_tune(self._h, pm, po, _stream_handle(stream), ctypes.byref(ms)),
+              "qed_batch_tune")
+        return ms.value
+
+    def info(self) -> dict:
+        b, t, n = ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
+        check(_lib.lib().qed_batch_info(self._h, ctypes.byref(b), ctypes.byref(t), ctypes.byref(n)),
+              "qed_batch_info")
+        return {"block": b.value, "work_target_flops": t.value, "n_items": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().qed_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

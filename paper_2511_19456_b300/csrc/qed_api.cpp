@@ -14,50 +14,7 @@
 #include "dag.hpp"
 #include "qed_types.h"
 
-namespace qed {
-struct KernelChoice {
-  void (*fn)(const KParams);
-  int team;
-};
-KernelChoice forward_kernel(int k, bool summed, bool mixed);
-KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
-cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
-                           cudaStream_t st, const KParams& p);
-}  // namespace qed
-
-using namespace qed;
-
-struct qed_plan_s {
-  int k = 0;
-  bool summed = true;
-  qed_precision prec = QED_FP64;
-  double mass = 1.0, charge = 1.0;
-  Schedule sc;
-  Instr* d_instr = nullptr;
-  Phase* d_phases = nullptr;
-  SetEntry* d_sets = nullptr;
-  KernelChoice kc{nullptr, 0};
-  int block = 0, grid = 0;
-  size_t smem = 0;
-  int team_bytes = 0;
-  int fixed_sin = 0, fixed_sout = 0, fixed_pol[8] = {0};
-  // adjoint: its own schedule (fewer kept levels where shared memory is short)
-  Schedule sc_adj;
-  Instr* d_instr_adj = nullptr;
-  Phase* d_phases_adj = nullptr;
-  SetEntry* d_sets_adj = nullptr;
-  KernelChoice kc_adj{nullptr, 0};
-  int block_adj = 0, grid_adj = 0;
-  size_t smem_adj = 0;
-  bool has_adj = false;
-  int device = 0;
-  // staging for qed_eval_host
-  double* d_stage = nullptr;
-  long long stage_cap = 0;    // points per buffer
-  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
-              ev_d2h[2] = {nullptr, nullptr};
-};
+#include "qed_plan.hpp"
 
 namespace {
 
@@ -72,11 +29,6 @@ void default_levels(int k, bool summed, int* ls, int* rs) {
   if (summed && k == 7) { *ls = 1; *rs = 1; }
 }
 
-qed_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return QED_OK;
-  if (e == cudaErrorMemoryAllocation) return QED_ENOMEM;
-  return QED_ECUDA;
-}
 
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
@@ -99,7 +51,15 @@ void free_plan(qed_plan_s* p) {
   delete p;
 }
 
-KParams make_params(const qed_plan_s* P, const double* mom, long long n, double* out) {
+}  // namespace
+
+qed_status qed::cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QED_OK;
+  if (e == cudaErrorMemoryAllocation) return QED_ENOMEM;
+  return QED_ECUDA;
+}
+
+KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, double* out) {
   KParams kp{};
   kp.mom = mom;
   kp.out = out;
@@ -121,6 +81,8 @@ KParams make_params(const qed_plan_s* P, const double* mom, long long n, double*
   for (int j = 0; j < 8; ++j) kp.fixed_pol_bits |= (unsigned)(P->fixed_pol[j] & 1) << j;
   return kp;
 }
+
+namespace {
 
 template <class T>
 cudaError_t upload(T** dst, const std::vector<T>& src) {

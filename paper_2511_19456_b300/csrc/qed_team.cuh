@@ -22,7 +22,7 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
   for (int off = (TEAM < 32 ? TEAM : 32) / 2; off > 0; off >>= 1)
     v += __shfl_xor_sync(0xffffffffu, v, off);
   if constexpr (TEAM > 32) {
-    const int w = threadIdx.x >> 5;
+    const int w = (threadIdx.x & (TEAM - 1)) >> 5;   // warp within the team
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[w] = v;
     __syncthreads();
@@ -239,8 +239,6 @@ __device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Rea
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;
   constexpr int R = N - H;
-  constexpr int NS = K + 3;
-  constexpr int NSUB = 1 << N;
   constexpr unsigned ALL = (1u << N) - 1;
   constexpr int NVL = SUMMED ? (1 << (H + 1)) : 1;
   constexpr int NVR = SUMMED ? (1 << (R + 1)) : 1;

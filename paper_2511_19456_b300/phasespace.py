@@ -141,13 +141,19 @@ def rambo_cm(n_points: int, masses, rs, seed: int) -> np.ndarray:
     # massive rescaling: find xi with sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = rs
     en = p[..., 0]
     xi = np.sqrt(np.maximum(0.0, 1.0 - (masses.sum() / rs) ** 2))
-    for _ in range(60):
-        e_i = np.sqrt(masses[None, :] ** 2 + (xi[:, None] * en) ** 2)
-        f = e_i.sum(axis=1) - rs
-        fp = np.sum(xi[:, None] * en * en / e_i, axis=1)
+    active = np.arange(n_points)
+    for _ in range(40):
+        # Newton steps on the points not yet converged (quadratic convergence
+        # from the massless start; stop at the rounding level)
+        x = xi[active]
+        e = en[active]
+        e_i = np.sqrt(masses[None, :] ** 2 + (x[:, None] * e) ** 2)
+        f = e_i.sum(axis=1) - rs[active]
+        fp = np.sum(x[:, None] * e * e / e_i, axis=1)
         step = f / fp
-        xi = xi - step
-        if np.max(np.abs(step)) < 1e-16:
+        xi[active] = x - step
+        active = active[np.abs(step) > 4e-16 * np.abs(x)]
+        if active.size == 0:
             break
     final = np.empty_like(p)
     final[..., 1:] = xi[:, None, None] * p[..., 1:]

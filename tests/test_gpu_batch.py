@@ -1,0 +1,81 @@
+"""Batched persistent launch: requests of k = 1..5 with uneven point counts in
+one graph launch give the same |M|^2 as one standalone launch per request
+(bit for bit: same per-point code), and match the oracle on samples."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2511_19456_b300 import Batch, Plan, _lib, phasespace as ps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REQS = [(5, 37, 6.0), (1, 3001, 1.0), (3, 999, 3.0), (2, 1, 2.5), (4, 257, 4.0), (1, 64, 8.0),
+        (5, 100, 3.0), (3, 0, 2.0), (4, 33, 7.0), (2, 4096, 1.5)]
+
+
+def make_inputs(seed0=700):
+    moms = [torch.from_numpy(ps.points(k, max(n, 1), om, seed0 + i))[:n].contiguous().cuda()
+            for i, (k, n, om) in enumerate(REQS)]
+    return moms
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_standalone_and_oracle(orc, precision):
+    plans = {k: Plan(k, precision=precision) for k in range(1, 6)}
+    moms = make_inputs()
+    batch = Batch([plans[k] for k, _, _ in REQS], [n for _, n, _ in REQS])
+    outs = batch.eval(moms)
+    torch.cuda.synchronize()
+    for (k, n, _), m, o in zip(REQS, moms, outs):
+        if n == 0:
+            continue
+        ref = plans[k].eval(m)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref), (k, n)
+    # oracle on a sample of each request
+    for (k, n, _), m, o in zip(REQS, moms, outs):
+        if n == 0:
+            continue
+        idx = np.unique(np.linspace(0, n - 1, min(n, 8)).astype(int))
+        mm = m.cpu().numpy()[idx]
+        r, kap = orc.m2(mm, kappa=True)
+        rel = np.abs(o.cpu().numpy()[idx] / r - 1)
+        tol = np.maximum(1e-12, 64 * 2.0 ** -53 * kap) if precision == "fp64" else \
+            32 * (2 * k + 1) * 2.0 ** -24 * np.maximum(kap, 1)
+        assert np.all(rel <= tol), (k, rel.max())
+
+
+def test_batch_tune_and_replay():
+    plans = {k: Plan(k, precision="mixed") for k in range(1, 6)}
+    moms = make_inputs(900)
+    batch = Batch([plans[k] for k, _, _ in REQS], [n for _, n, _ in REQS])
+    first = [o.clone() for o in batch.eval(moms)]
+    ms = batch.tune(moms)
+    info = batch.info()
+    assert ms > 0 and info["block"] in (64, 128, 256) and info["n_items"] > 0
+    outs = batch.outputs()
+    for _ in range(3):
+        batch.eval(moms, outs)
+    torch.cuda.synchronize()
+    for a, b in zip(first, outs):
+        assert torch.equal(a, b)
+
+
+def test_batch_rejects_bad_requests():
+    L = _lib.lib()
+    h = ctypes.c_void_p()
+    a, b = Plan(2), Plan(3, precision="mixed")
+    ph = (ctypes.c_void_p * 2)(a._h.value, b._h.value)
+    nn = (ctypes.c_longlong * 2)(10, 10)
+    assert L.qed_batch_create(ph, 2, nn, ctypes.byref(h)) == _lib.QED_EINVAL
+    f = Plan(2, summed=False, hel=[1, 1, 1, 1, 1])
+    ph = (ctypes.c_void_p * 1)(f._h.value)
+    assert L.qed_batch_create(ph, 1, nn, ctypes.byref(h)) == _lib.QED_EUNSUPPORTED
+    six = Plan(6)
+    ph = (ctypes.c_void_p * 1)(six._h.value)
+    assert L.qed_batch_create(ph, 1, nn, ctypes.byref(h)) == _lib.QED_EUNSUPPORTED
+    nn = (ctypes.c_longlong * 1)(-1)
+    ph = (ctypes.c_void_p * 1)(a._h.value)
+    assert L.qed_batch_create(ph, 1, nn, ctypes.byref(h)) == _lib.QED_EINVAL
