@@ -172,6 +172,33 @@ qed_status qed_batch_info(qed_batch_t batch, int* block, double* work_target, lo
 
 void qed_batch_destroy(qed_batch_t batch);
 
+/* Allocation-free batched evaluation.  The paper has no counterpart; this
+ * entry point serves callers that cannot allocate device memory when they
+ * evaluate:
+ *   - applications whose memory pool owns the device and forbids foreign
+ *     cudaMalloc calls;
+ *   - latency-critical loops that cannot afford the synchronisation a
+ *     cudaMalloc/cudaFree implies.
+ *
+ * Behaviour:
+ *   - It runs the same persistent kernel as qed_batch_eval on the same kinds
+ *     of request: spin-summed plans, k <= 5, all of one precision.
+ *   - The counter, request table and work items live in a static device
+ *     array of about 1.53 MiB, which every GPU that loads the library holds
+ *     until the process exits.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine. The
+ *     caller owns every input and output buffer.
+ *   - At most 256 requests; more return QED_EINVAL. Work items are made
+ *     larger until they fit the static table (65,536 items).
+ *   - The first call on a device looks up the array's device address. Make
+ *     that first call before any stream capture on that device.
+ *   - Every call shares the array and leaves its contents behind. The
+ *     counter is cleared on `stream` before each launch. Calls that overlap
+ *     on the GPU, on any stream, race with each other.
+ *   - Asynchronous on `stream`. */
+qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, const long long* n_points,
+                                 const double* const* d_momenta, double* const* d_out, void* stream);
+
 qed_status qed_dag_counts(int k, qed_dag_counts_t* out);
 
 const char* qed_status_string(qed_status status);

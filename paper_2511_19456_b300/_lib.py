@@ -80,6 +80,8 @@ SIGNATURES = [
     ("qed_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(_ll)]),
     ("qed_batch_destroy", None, [_vp]),
+    ("qed_batch_eval_static", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ll),
+                                             ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     ("qed_schedule_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ScheduleDesc), _vp, _vp, _vp]),
 ]

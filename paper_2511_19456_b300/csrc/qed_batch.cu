@@ -17,51 +17,8 @@
 #include <new>
 #include <vector>
 
-#include "qed_eval.cuh"
+#include "qed_batch.cuh"
 #include "qed_plan.hpp"
-
-namespace qed {
-
-struct BatchItem {
-  int32_t req;
-  int32_t k;
-  long long p0, p1;
-};
-
-struct BatchDesc {
-  KParams kp;
-};
-
-template <typename Real>
-__global__ void __launch_bounds__(256)
-qed_batch_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict__ items, int n_items,
-                 unsigned* counter) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= n_items) break;
-    const BatchItem item = items[it];
-    const KParams& kp = reqs[item.req].kp;
-    switch (item.k) {
-#define QED_BATCH_CASE(KK)                                                                       \
-  case KK: {                                                                                     \
-    constexpr int T = 1 << (KK + 1);                                                             \
-    eval_range<KK, true, Real, T, 1>(kp, item.p0, item.p1, (long long)(blockDim.x / T), smem);   \
-    break;                                                                                       \
-  }
-      QED_BATCH_CASE(1) QED_BATCH_CASE(2) QED_BATCH_CASE(3) QED_BATCH_CASE(4) QED_BATCH_CASE(5)
-#undef QED_BATCH_CASE
-      default: break;
-    }
-    __syncthreads();
-  }
-}
-
-}  // namespace qed
 
 using namespace qed;
 
