@@ -176,6 +176,101 @@ def run_reference(args, workload):
 METRIC = "|M|^2 points/s on 1 B300 (e gamma -> e + k gamma), FP32-mixed vs FP64, % of FLOP peak"
 
 
+def time_calls(fn, steps, warmup):
+    """CUDA-event time per call of fn() on the current stream (ms)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other(args):
+    """Measurement lines for the configurations other than the headline one.
+
+    compton_k6_fixed: FP64 and mixed forward, FP64 adjoint (qed_eval_grad).
+    compton_k7: mixed forward and adjoint on the full 131,072 points; the FP64
+      forward on a --fp64-points slice (one FP64 step of the full set takes
+      about 170 s).
+    batched: 64 requests, k = 1..5; the tuned graph launch (mixed and FP64)
+      against one launch per request (the plain FP64 GPU path).
+    """
+    import torch
+    from paper_2511_19456_b300 import Batch, Plan
+    torch.cuda.set_device(0)
+    res = {"workload": args.workload, "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
+    if args.workload == "batched":
+        reqs = ps.batched_requests()
+        moms = [torch.from_numpy(ps.points(r["k"], r["n_points"], r["omega"], r["seed"])).cuda()
+                for r in reqs]
+        n_tot = sum(r["n_points"] for r in reqs)
+        for prec in ("mixed", "fp64"):
+            plans = {k: Plan(k, precision=prec) for k in range(1, 6)}
+            flops = sum(plans[r["k"]].info()["flops_per_point"] * r["n_points"] for r in reqs)
+            batch = Batch([plans[r["k"]] for r in reqs], [r["n_points"] for r in reqs])
+            outs = batch.outputs()
+            tuned_ms = batch.tune(moms, outs) if prec == "mixed" else None
+            steps = args.steps if prec == "mixed" else 1
+            ms_b = time_calls(lambda: batch.eval(moms, outs), steps, 1)
+            seq_outs = [torch.empty_like(o) for o in outs]
+
+            def seq():
+                for r, m, o in zip(reqs, moms, seq_outs):
+                    plans[r["k"]].eval(m, o)
+            ms_s = time_calls(seq, steps, 1)
+            same = all(torch.equal(a, b) for a, b in zip(outs, seq_outs))
+            peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+            res[prec] = {"batched_points_per_s": n_tot / (ms_b * 1e-3), "batched_ms": ms_b,
+                         "sequential_points_per_s": n_tot / (ms_s * 1e-3), "sequential_ms": ms_s,
+                         "launches_sequential": len(reqs), "launches_batched": 1,
+                         "batched_tflops": flops / (ms_b * 1e-3) / 1e12,
+                         "batched_frac_of_peak": flops / (ms_b * 1e-3) / 1e12 / peak,
+                         "tune_best_ms": tuned_ms, "batch_info": batch.info(),
+                         "identical_to_sequential": same}
+        res.update(metric=METRIC, unit="points/s", value=res["mixed"]["batched_points_per_s"],
+                   config={"workload": "batched", "requests": len(reqs), "n_points": n_tot,
+                           "k": "1..5", "omega": "U[1,8]", "states": "summed"},
+                   speedup_batched_mixed_vs_sequential_fp64=res["fp64"]["sequential_ms"] / res["mixed"]["batched_ms"],
+                   speedup_batched_fp64_vs_sequential_fp64=res["fp64"]["sequential_ms"] / res["fp64"]["batched_ms"])
+        print(json.dumps(res), flush=True)
+        return
+    w = ps.WORKLOADS[args.workload]
+    k, n = w["k"], (args.n_points or w["n_points"])
+    hel = None if w["summed"] else w["hel"]
+    mom = torch.from_numpy(ps.points(k, n, w["omega"], w["seed"])).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    grad = torch.empty((n, k, 3), dtype=torch.float64, device="cuda")
+    for prec in ("mixed", "fp64"):
+        plan = Plan(k, summed=w["summed"], hel=hel, precision=prec)
+        info = plan.info()
+        nn = n if prec == "mixed" or args.fp64_points is None else min(n, args.fp64_points)
+        mm, oo, gg = mom[:nn], out[:nn], grad[:nn]
+        ms_f = time_calls(lambda: plan.eval(mm, oo), args.steps, args.warmup)
+        peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        leg = {"n_points": nn, "forward_points_per_s": nn / (ms_f * 1e-3), "forward_ms": ms_f,
+               "forward_tflops": info["flops_per_point"] * nn / (ms_f * 1e-3) / 1e12,
+               "forward_frac_of_peak": info["flops_per_point"] * nn / (ms_f * 1e-3) / 1e12 / peak}
+        try:
+            ms_g = time_calls(lambda: plan.eval_grad(mm, oo, gg), args.steps, args.warmup)
+            leg.update(adjoint_points_per_s=nn / (ms_g * 1e-3), adjoint_ms=ms_g,
+                       adjoint_over_forward_time=ms_g / ms_f)
+        except Exception as exc:  # plan without an adjoint in this precision
+            leg.update(adjoint=str(exc))
+        res[prec] = leg
+    res.update(metric=METRIC, unit="points/s", value=res["mixed"]["forward_points_per_s"],
+               config={"workload": args.workload, "k": k, "n_points": n, "omega": w["omega"],
+                       "states": "summed" if w["summed"] else "fixed"},
+               speedup_mixed_vs_fp64=res["mixed"]["forward_points_per_s"] / res["fp64"]["forward_points_per_s"])
+    print(json.dumps(res), flush=True)
+
+
 def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     import torch
     for _ in range(warmup):
@@ -200,9 +295,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS))
+    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched"],
+                    help="compton_k4 is the headline line; the others measure the other "
+                         "configurations (adjoint at k = 6, k = 7, the batched stream)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 path (default: --steps)")
+    ap.add_argument("--fp64-points", type=int, default=None,
+                    help="points of the FP64 legs of the non-headline workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
@@ -211,7 +310,14 @@ def main():
                     help="override the workload's point count (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload == "batched":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the batched stream is measured against the FP64 GPU path"}))
+            return
         run_reference(args, args.workload)
+        return
+    if args.workload != "compton_k4" and args.only is None:
+        run_other(args)
         return
 
     import torch
@@ -224,6 +330,7 @@ def main():
     barrier = (lambda: dist.barrier()) if ws > 1 else (lambda: None)
 
     from paper_2511_19456_b300 import Plan, measure_fma_peak
+    from paper_2511_19456_b300.distributed import max_over_ranks
 
     w = ps.WORKLOADS[args.workload]
     k = w["k"]
@@ -247,10 +354,7 @@ def main():
         with ClockSampler(local) as cs:
             ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier)
         launches += steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, device="cuda")
         pts = n * ws / (ms * 1e-3)
         flops = info["flops_per_point"]
         achieved = flops * n / (ms * 1e-3) / 1e12
@@ -296,10 +400,7 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.steps
         chunk = min(n, max(1 << 16, (n + 7) // 8))
         launches += args.steps * math.ceil(n / chunk)
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, device="cuda")
         e2e = {"value": n * ws / e2e_s, "unit": "points/s",
                "h2d_bytes_per_step": int(h_mom.numel() * 8),
                "d2h_bytes_per_step": int(h_out.numel() * 8)}
