@@ -41,7 +41,7 @@ def _worker(rank, world, port, values, results):
 def test_gloo_reductions(world):
     values = np.random.default_rng(0).random(1001)
     port = 29500 + world + (os.getpid() % 500)
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         results = m.dict()
         mp.spawn(_worker, args=(world, port, values, results), nprocs=world, join=True)
         got = dict(results)
