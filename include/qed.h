@@ -201,6 +201,44 @@ qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, const long 
 
 qed_status qed_dag_counts(int k, qed_dag_counts_t* out);
 
+/* Device-side phase-space points, the step before the |M|^2 path of a Monte
+ * Carlo event generator (the paper motivates the method by Monte Carlo
+ * sampling, Sec. III-E).  Writes points offset .. offset+n-1 of the seeded
+ * stream into d_momenta[n][k+3][4] (layout as above), with the same recipe
+ * and counter-based SplitMix64 draws as the host generator:
+ *   - k = 1: flat two-body, uniform in the CM solid angle;
+ *   - k >= 2: RAMBO (Kleiss, Stirling, Ellis 1986) with the electron
+ *     massive.
+ * The lab frame has e- at rest and the photon along +z with energy omega.
+ * d_weight[n] (may be NULL) receives the phase-space weight:
+ *   - the measure is (2 pi)^4 delta^4 prod d^3p / ((2 pi)^3 2E);
+ *   - massless RAMBO weight times the massive correction factor.
+ * Errors: QED_EINVAL (k outside [1,7], omega or mass <= 0, offset or
+ * n < 0, NULL or misaligned buffers).  Asynchronous. */
+qed_status qed_generate(int k, double omega, double mass, unsigned long long seed, long long offset,
+                        long long n, double* d_momenta, double* d_weight, void* stream);
+
+/* Monte Carlo estimate of the total cross section
+ *   sigma = 1/(4 m omega) * 1/4 * 1/k! * <w * sum|M|^2>
+ * for a spin-summed plan. The factors are the flux of an e- at rest, the
+ * average over the initial helicity and polarisation states, and the
+ * identical outgoing photons.
+ * Procedure: generate points offset .. offset+n-1 of stream `seed`, in
+ * chunks of `chunk` points, evaluate each chunk, and accumulate
+ * sum(w |M|^2) and sum((w |M|^2)^2) on the device in d_acc[2].
+ * Caller-owned device buffers:
+ *   - d_momenta[chunk][k+3][4];
+ *   - d_weight[chunk];
+ *   - d_m2[chunk];
+ *   - d_acc[2].
+ * Outputs: sigma, its standard error sigma_err and the two raw sums (any of
+ * them may be NULL). Partial sums from several ranks combine by adding the
+ * raw sums. Synchronises `stream`. */
+qed_status qed_cross_section(qed_plan_t plan, double omega, unsigned long long seed, long long offset,
+                             long long n, long long chunk, double* d_momenta, double* d_weight,
+                             double* d_m2, double* d_acc, void* stream, double* sigma, double* sigma_err,
+                             double* sum_wm2, double* sum_wm2_sq);
+
 const char* qed_status_string(qed_status status);
 
 /* Measured FMA-pipe peak of the current device in TFLOP/s: FP64 for

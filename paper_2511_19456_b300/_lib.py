@@ -82,6 +82,10 @@ SIGNATURES = [
     ("qed_batch_destroy", None, [_vp]),
     ("qed_batch_eval_static", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ll),
                                              ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    ("qed_generate", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong,
+                                    _ll, _ll, _vp, _vp, _vp]),
+    ("qed_cross_section", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_ulonglong, _ll, _ll, _ll, _vp, _vp,
+                                         _vp, _vp, _vp] + [ctypes.POINTER(ctypes.c_double)] * 4),
     ("qed_schedule_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ScheduleDesc), _vp, _vp, _vp]),
 ]

@@ -231,3 +231,39 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def generate(k: int, n_points: int, omega: float, seed: int, offset: int = 0, mass: float = 1.0,
+             weights: bool = False, stream=None):
+    """Phase-space points (and weights) generated on the device; the same
+    recipe and random draws as phasespace.points()."""
+    torch = _torch()
+    mom = torch.empty((n_points, k + 3, 4), dtype=torch.float64, device="cuda")
+    w = torch.empty(n_points, dtype=torch.float64, device="cuda") if weights else None
+    check(_lib.lib().qed_generate(int(k), float(omega), float(mass), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                  int(offset), int(n_points), ctypes.c_void_p(mom.data_ptr()),
+                                  ctypes.c_void_p(w.data_ptr() if w is not None else None),
+                                  _stream_handle(stream)), "qed_generate")
+    return (mom, w) if weights else mom
+
+
+def cross_section(plan, omega: float, n_points: int, seed: int, offset: int = 0,
+                  chunk: int = 1 << 20, stream=None) -> dict:
+    """Monte Carlo total cross section of a spin-summed plan (e = m = 1 units
+    unless the plan says otherwise): generated on the device, evaluated, and
+    reduced on the device."""
+    torch = _torch()
+    chunk = int(min(chunk, n_points))
+    k = plan.k
+    mom = torch.empty((chunk, k + 3, 4), dtype=torch.float64, device="cuda")
+    w = torch.empty(chunk, dtype=torch.float64, device="cuda")
+    m2 = torch.empty(chunk, dtype=torch.float64, device="cuda")
+    acc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    out = [ctypes.c_double() for _ in range(4)]
+    check(_lib.lib().qed_cross_section(plan._h, float(omega), int(seed) & 0xFFFFFFFFFFFFFFFF, int(offset),
+                                       int(n_points), chunk, ctypes.c_void_p(mom.data_ptr()),
+                                       ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(m2.data_ptr()),
+                                       ctypes.c_void_p(acc.data_ptr()), _stream_handle(stream),
+                                       *[ctypes.byref(o) for o in out]), "qed_cross_section")
+    return {"sigma": out[0].value, "sigma_err": out[1].value, "sum_wm2": out[2].value,
+            "sum_wm2_sq": out[3].value, "n_points": int(n_points)}
