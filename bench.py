@@ -271,6 +271,52 @@ def run_other(args):
     print(json.dumps(res), flush=True)
 
 
+def run_rewrite_compare(args):
+    """The distributively rewritten DAG against the plain (node-reduced) DAG,
+    forward pass, both precisions, on the headline workloads.  For each leg:
+    points/s of both DAGs on the same points, the speed-up, and the largest
+    relative difference between them.  The plain FP64 pass at k = 7 runs on a
+    slice (one full step takes minutes)."""
+    import torch
+    from paper_2511_19456_b300 import Plan
+    torch.cuda.set_device(0)
+    res = {"workload": "rewrite_vs_plain", "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+           "metric": METRIC, "unit": "points/s"}
+    slices = {"compton_k4": (None, None), "compton_k6_fixed": (None, 16384), "compton_k7": (16384, 2048)}
+    for wname, (n_mixed, n_fp64) in slices.items():
+        w = ps.WORKLOADS[wname]
+        k = w["k"]
+        hel = None if w["summed"] else w["hel"]
+        mom_all = torch.from_numpy(ps.points(k, w["n_points"], w["omega"], w["seed"])).cuda()
+        legs = {}
+        for prec, n_cut in (("mixed", n_mixed), ("fp64", n_fp64)):
+            n = w["n_points"] if n_cut is None else n_cut
+            mom = mom_all[:n]
+            leg = {"n_points": n}
+            outs = {}
+            for dag in ("rewrite", "plain"):
+                plan = Plan(k, summed=w["summed"], hel=hel, precision=prec, rewrite=(dag == "rewrite"))
+                out = torch.empty(n, dtype=torch.float64, device="cuda")
+                steps = args.steps if dag == "rewrite" else max(1, min(args.steps, 3))
+                ms = time_calls(lambda: plan.eval(mom, out), steps, 1 if dag == "plain" else args.warmup)
+                leg[dag] = {"ms": ms, "points_per_s": n / (ms * 1e-3),
+                            "flops_per_point": plan.info()["flops_per_point"]}
+                outs[dag] = out
+            leg["speedup_rewrite_vs_plain"] = leg["plain"]["ms"] / leg["rewrite"]["ms"]
+            leg["max_rel_diff"] = float(((outs["rewrite"] / outs["plain"]) - 1).abs().max())
+            legs[prec] = leg
+        # the full workload through the rewrite: the headline rate of this DAG
+        for prec in ("mixed", "fp64"):
+            plan = Plan(k, summed=w["summed"], hel=hel, precision=prec, rewrite=True)
+            out = torch.empty(w["n_points"], dtype=torch.float64, device="cuda")
+            ms = time_calls(lambda: plan.eval(mom_all, out), args.steps, args.warmup)
+            legs[prec]["rewrite_full_points_per_s"] = w["n_points"] / (ms * 1e-3)
+        res[wname] = legs
+    res["value"] = res["compton_k4"]["mixed"]["rewrite_full_points_per_s"]
+    res["config"] = {"workload": "rewrite_vs_plain", "k": "4 (summed), 6 (fixed), 7 (summed)"}
+    print(json.dumps(res), flush=True)
+
+
 def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     import torch
     for _ in range(warmup):
@@ -295,7 +341,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched"],
+    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched", "rewrite_vs_plain"],
                     help="compton_k4 is the headline line; the others measure the other "
                          "configurations (adjoint at k = 6, k = 7, the batched stream)")
     ap.add_argument("--fp64-steps", type=int, default=None,
@@ -310,11 +356,14 @@ def main():
                     help="override the workload's point count (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
-        if args.workload == "batched":
+        if args.workload in ("batched", "rewrite_vs_plain"):
             print(json.dumps({"impl": "reference", "unavailable":
                               "the batched stream is measured against the FP64 GPU path"}))
             return
         run_reference(args, args.workload)
+        return
+    if args.workload == "rewrite_vs_plain":
+        run_rewrite_compare(args)
         return
     if args.workload != "compton_k4" and args.only is None:
         run_other(args)

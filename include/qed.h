@@ -118,6 +118,20 @@ typedef struct {
 qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
                            qed_precision precision, qed_plan_t* out);
 
+/* As qed_plan_create, for the distributively rewritten DAG: the term
+ * rewriting the paper proposes as a further node operation (App. C). The
+ * joins of a photon set S share their propagator, so
+ *   sum_{a,b} R'_b L_a = (sum_b R'_b)(sum_a L_a).
+ * Applied recursively, this collapses the currents of all orderings of a
+ * photon subset T into one current per subset:
+ *   J_T = sum_{j in T} eps/_j S(Q_{T\j}) J_{T\j}.
+ * The value is the same |M|^2. The cost grows exponentially with the number
+ * of photons instead of factorially. qed_eval and qed_plan_info work on such
+ * plans. qed_eval_grad and the batched entry points return
+ * QED_EUNSUPPORTED. */
+qed_status qed_plan_create_rewrite(const qed_process* process, const qed_spin_cfg* spin,
+                                   qed_precision precision, qed_plan_t* out);
+
 qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 
 /* out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4
@@ -261,6 +275,14 @@ typedef struct {
 
 qed_status qed_schedule_export(int k, int summed, qed_schedule_desc_t* desc, void* instr,
                                void* phases, void* sets);
+
+/* The same for the rewritten DAG. Instructions are 48 bytes (SumInstr in
+ * csrc/dag.hpp: one node summing up to 4 vertex terms). group is the number of
+ * photon sets whose leaves one set phase builds; 0 picks the default. Each set
+ * entry's phase0 names its group's phase. Returns QED_EINVAL when k is
+ * outside 1..7 or group < 0. */
+qed_status qed_rewrite_schedule_export(int k, int summed, int group, qed_schedule_desc_t* desc,
+                                       void* instr, void* phases, void* sets);
 
 #ifdef __cplusplus
 }

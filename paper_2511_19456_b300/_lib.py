@@ -64,6 +64,8 @@ _ll = ctypes.c_longlong
 SIGNATURES = [
     ("qed_plan_create", ctypes.c_int, [ctypes.POINTER(Process), ctypes.POINTER(SpinCfg),
                                        ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("qed_plan_create_rewrite", ctypes.c_int, [ctypes.POINTER(Process), ctypes.POINTER(SpinCfg),
+                                               ctypes.c_int, ctypes.POINTER(_vp)]),
     ("qed_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
     ("qed_eval", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),
     ("qed_eval_grad", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, _vp]),
@@ -86,6 +88,8 @@ SIGNATURES = [
                                     _ll, _ll, _vp, _vp, _vp]),
     ("qed_cross_section", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_ulonglong, _ll, _ll, _ll, _vp, _vp,
                                          _vp, _vp, _vp] + [ctypes.POINTER(ctypes.c_double)] * 4),
+    ("qed_rewrite_schedule_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ScheduleDesc), _vp, _vp, _vp]),
     ("qed_schedule_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ScheduleDesc), _vp, _vp, _vp]),
 ]

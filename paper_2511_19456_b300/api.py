@@ -37,7 +37,7 @@ class Plan:
     """
 
     def __init__(self, k: int, summed: bool = True, hel=None, precision: str = "fp64",
-                 mass: float = 1.0, charge: float = 1.0):
+                 mass: float = 1.0, charge: float = 1.0, rewrite: bool = False):
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {sorted(_PREC)}")
         L = _lib.lib()
@@ -50,8 +50,10 @@ class Plan:
             for i, v in enumerate(hel):
                 spin.hel[i] = int(v)
         handle = ctypes.c_void_p()
-        check(L.qed_plan_create(ctypes.byref(proc), ctypes.byref(spin), _PREC[precision],
-                                ctypes.byref(handle)), "qed_plan_create")
+        create = L.qed_plan_create_rewrite if rewrite else L.qed_plan_create
+        check(create(ctypes.byref(proc), ctypes.byref(spin), _PREC[precision], ctypes.byref(handle)),
+              "qed_plan_create")
+        self.rewrite = bool(rewrite)
         self._h = handle
         self.k = int(k)
         self.summed = bool(summed)
@@ -143,21 +145,34 @@ PHASE_DTYPE = np.dtype([("beg", "<i4", 2), ("cnt", "<i4", 2), ("level", "<i4", 2
 SET_DTYPE = np.dtype([("mask", "<u4"), ("phase0", "<i4"), ("leaf_l", "<i4"), ("leaf_r", "<i4")])
 
 
-def schedule_export(k: int, summed: bool) -> dict:
-    """The linear schedule the kernels execute, as numpy structured arrays."""
+SUM_INSTR_DTYPE = np.dtype([("dst", "<i4"), ("src", "<i4", 4), ("photon", "u1", 4), ("rank", "u1", 4),
+                            ("nterms", "u1"), ("side", "u1"), ("level", "u1"), ("pad0", "u1"),
+                            ("post", "<u2"), ("pad1", "<u2"), ("pad2", "<i4", 3)])
+
+
+def schedule_export(k: int, summed: bool, rewrite: bool = False, group: int = 0) -> dict:
+    """The linear schedule the kernels execute, as numpy structured arrays.
+    rewrite: the distributively rewritten DAG; group: its photon sets per set
+    phase (0: the default)."""
     L = _lib.lib()
     d = _lib.ScheduleDesc()
-    check(L.qed_schedule_export(int(k), int(summed), ctypes.byref(d), None, None, None),
-          "qed_schedule_export")
-    instr = np.zeros(d.n_instr, dtype=INSTR_DTYPE)
+    if rewrite:
+        def fn(*a):
+            return L.qed_rewrite_schedule_export(a[0], a[1], int(group), *a[2:])
+    else:
+        fn = L.qed_schedule_export
+    check(fn(int(k), int(summed), ctypes.byref(d), None, None, None), "qed_schedule_export")
+    instr = np.zeros(d.n_instr, dtype=SUM_INSTR_DTYPE if rewrite else INSTR_DTYPE)
     phases = np.zeros(d.n_phases, dtype=PHASE_DTYPE)
     sets = np.zeros(d.n_sets, dtype=SET_DTYPE)
-    check(L.qed_schedule_export(int(k), int(summed), ctypes.byref(d),
-                                instr.ctypes.data_as(ctypes.c_void_p),
-                                phases.ctypes.data_as(ctypes.c_void_p),
-                                sets.ctypes.data_as(ctypes.c_void_p)), "qed_schedule_export")
+    check(fn(int(k), int(summed), ctypes.byref(d),
+             instr.ctypes.data_as(ctypes.c_void_p),
+             phases.ctypes.data_as(ctypes.c_void_p),
+             sets.ctypes.data_as(ctypes.c_void_p)), "qed_schedule_export")
     out = {f: getattr(d, f) for f, _ in _lib.ScheduleDesc._fields_}
     out.update(instr=instr, phases=phases, sets=sets)
+    if rewrite:
+        out["group"] = int(np.sum(sets["phase0"] == sets["phase0"][0]))
     return out
 
 

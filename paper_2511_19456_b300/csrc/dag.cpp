@@ -401,4 +401,135 @@ Schedule build_schedule(int k, bool summed, int ls, int rs) {
   return sc;
 }
 
+static long long n_choose(int n, int m) {
+  long long c = 1;
+  for (int i = 1; i <= m; ++i) c = c * (n - m + i) / i;
+  return c;
+}
+
+int rewrite_default_group(int k, bool summed, int team) {
+  const int n = k + 1, h = (n + 1) / 2, r = n - h;
+  const int per_set = nvar(summed, h) + nvar(summed, r);
+  const int nsets = (int)n_choose(n, h);
+  const int g = std::max(1, std::min(nsets, (4 * team + per_set - 1) / per_set));
+  const int groups = (nsets + g - 1) / g;
+  return (nsets + groups - 1) / groups;   // groups of nearly equal size
+}
+
+RwSchedule build_rewrite_schedule(int k, bool summed, int group) {
+  if (k < 1 || k > 7) throw std::runtime_error("k out of range");
+  if (group <= 0) group = rewrite_default_group(k, summed, summed ? 1 << (k + 1) : 32);
+  RwSchedule sc;
+  sc.k = k;
+  sc.n = k + 1;
+  sc.h = (sc.n + 1) / 2;
+  sc.r = sc.n - sc.h;
+  sc.summed = summed;
+  const int n = sc.n, h = sc.h, r = sc.r;
+  const uint32_t all = (1u << n) - 1;
+  // node index of (side, subset) for the kept levels
+  std::vector<int> idx[2];
+  idx[0].assign(1u << n, -1);
+  idx[1].assign(1u << n, -1);
+  int next = 0;
+  auto make = [&](int side, uint32_t T, int dst, bool post) {
+    SumInstr in{};
+    in.dst = dst;
+    in.side = (uint8_t)side;
+    in.level = (uint8_t)__builtin_popcount(T);
+    int t = 0;
+    for (int j = 0; j < n; ++j) {
+      if (!(T & (1u << j))) continue;
+      const uint32_t par = T & ~(1u << j);
+      in.src[t] = par ? idx[side][par] : -1;
+      if (par && in.src[t] < 0) throw std::runtime_error("rewrite: missing input node");
+      in.photon[t] = (uint8_t)j;
+      in.rank[t] = (uint8_t)__builtin_popcount(T & ((1u << j) - 1));
+      ++t;
+    }
+    for (; t < 4; ++t) { in.src[t] = -1; in.photon[t] = 0; in.rank[t] = 0; }
+    in.nterms = (uint8_t)in.level;
+    if (side == 0) in.post = post ? (uint16_t)T : 0;
+    else in.post = (uint16_t)(all & ~T);
+    return in;
+  };
+  const int nsp = std::max(h - 1, r - 1);
+  for (int lev = 1; lev <= nsp; ++lev) {
+    Phase ph{};
+    int slot = 0;
+    for (int side = 0; side < 2; ++side) {
+      const int lim = side == 0 ? h - 1 : r - 1;
+      if (lev > lim) continue;
+      const int beg = (int)sc.instr.size();
+      int cnt = 0;
+      for (uint32_t T = 1; T <= all; ++T) {
+        if (__builtin_popcount(T) != lev) continue;
+        idx[side][T] = next;
+        sc.instr.push_back(make(side, T, next, true));
+        next += nvar(summed, lev);
+        ++cnt;
+      }
+      ph.beg[slot] = beg;
+      ph.cnt[slot] = cnt;
+      ph.level[slot] = lev;
+      ++slot;
+    }
+    sc.phases.push_back(ph);
+  }
+  sc.n_stored_phases = (int)sc.phases.size();
+  sc.stored_currents = next;
+  sc.n_set_phases = 1;
+  std::vector<uint32_t> masks;
+  for (uint32_t S = 0; S <= all; ++S)
+    if (__builtin_popcount(S) == h) masks.push_back(S);
+  const int nsets = (int)masks.size();
+  sc.group = std::min(group, nsets);
+  const int nvh = nvar(summed, h), nvr = nvar(summed, r);
+  for (int g0 = 0; g0 < nsets; g0 += sc.group) {
+    const int g1 = std::min(nsets, g0 + sc.group);
+    Phase ph{};
+    ph.beg[0] = (int)sc.instr.size();
+    ph.cnt[0] = g1 - g0;
+    ph.level[0] = h;
+    for (int i = g0; i < g1; ++i) sc.instr.push_back(make(0, masks[i], next + (i - g0) * nvh, false));
+    ph.beg[1] = (int)sc.instr.size();
+    ph.cnt[1] = g1 - g0;
+    ph.level[1] = r;
+    const int rbase = next + (g1 - g0) * nvh;
+    for (int i = g0; i < g1; ++i) sc.instr.push_back(make(1, all & ~masks[i], rbase + (i - g0) * nvr, true));
+    for (int i = g0; i < g1; ++i) {
+      SetEntry se{};
+      se.mask = masks[i];
+      se.phase0 = (int)sc.phases.size();
+      se.leaf_l = next + (i - g0) * nvh;
+      se.leaf_r = rbase + (i - g0) * nvr;
+      sc.sets.push_back(se);
+    }
+    sc.phases.push_back(ph);
+    ++sc.n_groups;
+  }
+  sc.local_currents = sc.group * (nvh + nvr);
+  // counts and FLOPs of the rewritten DAG (each subset node once; the
+  // per-set leaves are the level-h / level-r nodes)
+  const long long P = summed ? (1ll << (n + 2)) : 1;
+  long long fl = ((1ll << n) - 2) * FLOP_SUBSET + 4ll * FLOP_SPINOR + 2ll * n * FLOP_POL + P * FLOP_SQUARE;
+  for (int side = 0; side < 2; ++side) {
+    const int top = side == 0 ? h : r;
+    for (uint32_t T = 1; T <= all; ++T) {
+      const int lev = __builtin_popcount(T);
+      if (lev > top) continue;
+      const long long nv = nvar(summed, lev);
+      sc.nodes += nv;
+      sc.terms += nv * lev;
+      fl += nv * (lev * FLOP_V + (lev - 1) * 8);
+      const bool post = side == 1 || lev < top;
+      if (post) { sc.s1_nodes += nv; fl += nv * FLOP_S1; }
+    }
+  }
+  sc.joins = (long long)nsets * P;
+  fl += sc.joins * FLOP_JOIN;
+  sc.flops_algorithmic = fl;
+  return sc;
+}
+
 }  // namespace qed

@@ -101,6 +101,53 @@ struct Schedule {
 
 int nvar(bool summed, int level);
 
+// ------------------------------------------------ distributive rewrite
+// Term rewriting of the reduced DAG (the paper proposes it as a further node
+// operation, App. C): the S2 joins of one photon set S share their
+// propagator, so by distributivity sum_{a,b} R'_b L_a = (sum_b R'_b)(sum_a L_a);
+// applied recursively, the currents of all orderings of a photon subset T
+// collapse into one current per subset,
+//   J_T = sum_{j in T} eps/_j S(Q_{T \ j}) J_{T \ j}   (column, from u),
+// and likewise for row currents from ubar.  A node of the rewritten DAG is a
+// subset; it sums one vertex term per photon of the subset and is then
+// propagated.  One join per photon set remains.
+struct SumInstr {
+  int32_t dst;
+  int32_t src[4];       // input node of each term (-1: the external spinor)
+  uint8_t photon[4];
+  uint8_t rank[4];      // rank of the term's photon within the node's set
+  uint8_t nterms;
+  uint8_t side;
+  uint8_t level;
+  uint8_t pad0;
+  uint16_t post;        // propagator applied to the sum (0 = none)
+  uint16_t pad1;
+  int32_t pad2[3];
+};
+static_assert(sizeof(SumInstr) == 48, "SumInstr layout");
+
+struct RwSchedule {
+  int k = 0, n = 0, h = 0, r = 0;
+  bool summed = true;
+  int group = 1;                    // photon sets whose leaves one set phase builds
+  int n_groups = 0;
+  int stored_currents = 0, local_currents = 0;
+  int n_stored_phases = 0, n_set_phases = 0;
+  std::vector<SumInstr> instr;
+  std::vector<Phase> phases;
+  std::vector<SetEntry> sets;
+  long long nodes = 0, terms = 0, s1_nodes = 0, joins = 0;   // times spin variants
+  long long flops_algorithmic = 0;
+};
+
+// group: number of photon sets handled per set phase (their leaves are built
+// together, then their joins run without a barrier in between); 0 picks
+// rewrite_default_group.
+RwSchedule build_rewrite_schedule(int k, bool summed, int group = 0);
+// Enough leaf instructions per set phase for about four per thread of a team
+// of `team` threads.
+int rewrite_default_group(int k, bool summed, int team);
+
 // Build the reduced DAG of process k and linearise it.  ls/rs: number of
 // left/right levels stored for the whole point (at most h-1 / r-1); deeper
 // levels are rebuilt for each photon set.  Throws std::runtime_error when the

@@ -40,6 +40,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_instr_adj);
   cudaFree(p->d_phases_adj);
   cudaFree(p->d_sets_adj);
+  cudaFree(p->d_sinstr);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
@@ -65,13 +66,24 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.out = out;
   kp.n = n;
   kp.instr = P->d_instr;
+  kp.sinstr = P->d_sinstr;
   kp.phases = P->d_phases;
   kp.sets = P->d_sets;
-  kp.n_stored_phases = P->sc.n_stored_phases;
-  kp.n_set_phases = P->sc.n_set_phases;
-  kp.n_sets = (int)P->sc.sets.size();
-  kp.ncur = P->sc.stored_currents + P->sc.local_currents;
-  kp.ncur_stored = P->sc.stored_currents;
+  if (P->rewrite) {
+    kp.n_stored_phases = P->rsc.n_stored_phases;
+    kp.n_set_phases = P->rsc.n_set_phases;
+    kp.n_sets = (int)P->rsc.sets.size();
+    kp.ncur = P->rsc.stored_currents + P->rsc.local_currents;
+    kp.ncur_stored = P->rsc.stored_currents;
+    kp.set_group = P->rsc.group;
+  } else {
+    kp.set_group = 1;
+    kp.n_stored_phases = P->sc.n_stored_phases;
+    kp.n_set_phases = P->sc.n_set_phases;
+    kp.n_sets = (int)P->sc.sets.size();
+    kp.ncur = P->sc.stored_currents + P->sc.local_currents;
+    kp.ncur_stored = P->sc.stored_currents;
+  }
   kp.team_bytes = P->team_bytes;
   kp.mass = P->mass;
   kp.coupling = std::pow(P->charge, 2.0 * (P->k + 1));
@@ -189,8 +201,9 @@ qed_status qed_dag_counts(int k, qed_dag_counts_t* out) {
   return QED_OK;
 }
 
-qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
-                           qed_precision precision, qed_plan_t* out) {
+namespace {
+qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed_precision precision,
+                       bool rewrite, qed_plan_t* out) {
   if (!process || !spin || !out) return QED_EINVAL;
   const int k = process->k;
   if (k < 1 || k > 7) return QED_EINVAL;
@@ -217,8 +230,34 @@ qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
   }
   int ls, rs;
   default_levels(k, P->summed, &ls, &rs);
+  P->rewrite = rewrite;
+  const bool mixed = precision == QED_MIXED;
+  P->kc = rewrite ? rewrite_kernel(k, P->summed, mixed) : forward_kernel(k, P->summed, mixed);
+  if (!P->kc.fn) { delete P; return QED_EUNSUPPORTED; }
+  int dev_smem = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e != cudaSuccess) { delete P; return cuda_status(e); }
   try {
     P->sc = build_schedule(k, P->summed, ls, rs);
+    if (rewrite) {
+      // photon sets per set phase: as many as keep a team's shared memory
+      // within half the SM's (two resident teams), or within all of it when
+      // the stored currents alone exceed that
+      const int real = mixed ? 4 : 8;
+      int g = rewrite_default_group(k, P->summed, P->kc.team);
+      const RwSchedule one = build_rewrite_schedule(k, P->summed, 1);
+      const int budget = team_layout(k, real, one.stored_currents + one.local_currents).bytes <= dev_smem / 2
+                             ? dev_smem / 2 : dev_smem;
+      for (;;) {
+        P->rsc = build_rewrite_schedule(k, P->summed, g);
+        if (g == 1 || team_layout(k, real, P->rsc.stored_currents + P->rsc.local_currents).bytes <= budget)
+          break;
+        g = (g + 1) / 2;
+      }
+    }
   } catch (const std::bad_alloc&) {
     delete P;
     return QED_ENOMEM;
@@ -226,22 +265,22 @@ qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
     delete P;
     return QED_EUNSUPPORTED;
   }
-  cudaError_t e = cudaGetDevice(&P->device);
-  if (e == cudaSuccess) e = upload(&P->d_instr, P->sc.instr);
-  if (e == cudaSuccess) e = upload(&P->d_phases, P->sc.phases);
-  if (e == cudaSuccess) e = upload(&P->d_sets, P->sc.sets);
+  if (rewrite) {
+    if (e == cudaSuccess) e = upload(&P->d_sinstr, P->rsc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases, P->rsc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets, P->rsc.sets);
+  } else {
+    if (e == cudaSuccess) e = upload(&P->d_instr, P->sc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases, P->sc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets, P->sc.sets);
+  }
   if (e != cudaSuccess) { free_plan(P); return cuda_status(e); }
-  const bool mixed = precision == QED_MIXED;
-  P->kc = forward_kernel(k, P->summed, mixed);
-  if (!P->kc.fn) { free_plan(P); return QED_EUNSUPPORTED; }
-  const int ncur = P->sc.stored_currents + P->sc.local_currents;
+  const int ncur = rewrite ? P->rsc.stored_currents + P->rsc.local_currents
+                           : P->sc.stored_currents + P->sc.local_currents;
   TeamLayout L = team_layout(k, mixed ? 4 : 8, ncur);
   P->team_bytes = L.bytes;
   P->block = P->kc.team > 32 ? P->kc.team : 128;
   P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
-  int dev_smem = 0, sms = 0;
-  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   while (P->smem > (size_t)dev_smem && P->block > P->kc.team && P->block > 32) {
     P->block /= 2;
     P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
@@ -255,10 +294,23 @@ qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
                                                       P->smem);
   if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
   P->grid = per_sm * sms;
-  qed_status as = setup_adjoint(P, mixed, dev_smem, sms);
-  if (as != QED_OK) { free_plan(P); return as; }
+  if (!rewrite) {
+    qed_status as = setup_adjoint(P, mixed, dev_smem, sms);
+    if (as != QED_OK) { free_plan(P); return as; }
+  }
   *out = P;
   return QED_OK;
+}
+}  // namespace
+
+qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
+                           qed_precision precision, qed_plan_t* out) {
+  return create_plan(process, spin, precision, false, out);
+}
+
+qed_status qed_plan_create_rewrite(const qed_process* process, const qed_spin_cfg* spin,
+                                   qed_precision precision, qed_plan_t* out) {
+  return create_plan(process, spin, precision, true, out);
 }
 
 qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
@@ -277,8 +329,14 @@ qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
   info->v_nodes = sc.v_nodes;
   info->s1_nodes = sc.s1_nodes;
   info->s2_nodes = sc.s2_nodes;
-  info->flops_per_point = sc.flops_algorithmic;
-  info->flops_executed_per_point = sc.flops_executed;
+  info->flops_per_point = P->rewrite ? P->rsc.flops_algorithmic : sc.flops_algorithmic;
+  info->flops_executed_per_point = P->rewrite ? P->rsc.flops_algorithmic : sc.flops_executed;
+  if (P->rewrite) {
+    info->nodes_reduced = P->rsc.nodes;      // subset nodes times spin variants
+    info->v_nodes = P->rsc.terms;
+    info->s1_nodes = P->rsc.s1_nodes;
+    info->s2_nodes = P->rsc.joins;
+  }
   info->flops_literal_s2_per_point = sc.flops_literal_s2;
   info->team_threads = P->kc.team;
   info->smem_bytes_per_team = P->team_bytes;
@@ -406,6 +464,30 @@ qed_status qed_schedule_export(int k, int summed, qed_schedule_desc_t* desc, voi
   desc->flops_algorithmic = sc.flops_algorithmic;
   desc->flops_executed = sc.flops_executed;
   if (instr) std::memcpy(instr, sc.instr.data(), sc.instr.size() * sizeof(Instr));
+  if (phases) std::memcpy(phases, sc.phases.data(), sc.phases.size() * sizeof(Phase));
+  if (sets) std::memcpy(sets, sc.sets.data(), sc.sets.size() * sizeof(SetEntry));
+  return QED_OK;
+}
+
+qed_status qed_rewrite_schedule_export(int k, int summed, int group, qed_schedule_desc_t* desc,
+                                       void* instr, void* phases, void* sets) {
+  if (!desc || k < 1 || k > 7 || group < 0) return QED_EINVAL;
+  RwSchedule sc;
+  try {
+    sc = build_rewrite_schedule(k, summed != 0, group);
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  std::memset(desc, 0, sizeof(*desc));
+  desc->k = sc.k; desc->n = sc.n; desc->h = sc.h; desc->r = sc.r; desc->summed = sc.summed ? 1 : 0;
+  desc->n_left_leaves = 1; desc->n_right_leaves = 1;
+  desc->stored_currents = sc.stored_currents; desc->local_currents = sc.local_currents;
+  desc->n_stored_phases = sc.n_stored_phases; desc->n_set_phases = sc.n_set_phases;
+  desc->n_sets = (int)sc.sets.size(); desc->n_instr = (int)sc.instr.size();
+  desc->n_phases = (int)sc.phases.size();
+  desc->flops_algorithmic = sc.flops_algorithmic;
+  desc->flops_executed = sc.flops_algorithmic;
+  if (instr) std::memcpy(instr, sc.instr.data(), sc.instr.size() * sizeof(SumInstr));
   if (phases) std::memcpy(phases, sc.phases.data(), sc.phases.size() * sizeof(Phase));
   if (sets) std::memcpy(sets, sc.sets.data(), sc.sets.size() * sizeof(SetEntry));
   return QED_OK;

@@ -147,7 +147,7 @@ qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long*
   for (int r = 0; r < n_req; ++r) {
     if (!plans[r] || n_points[r] < 0) return QED_EINVAL;
     if ((plans[r]->prec == QED_MIXED) != mixed) return QED_EINVAL;
-    if (!plans[r]->summed || plans[r]->k > kMaxBatchK) return QED_EUNSUPPORTED;
+    if (!plans[r]->summed || plans[r]->k > kMaxBatchK || plans[r]->rewrite) return QED_EUNSUPPORTED;
   }
   qed_batch_s* b = new (std::nothrow) qed_batch_s();
   if (!b) return QED_ENOMEM;

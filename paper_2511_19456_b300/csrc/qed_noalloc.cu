@@ -61,7 +61,7 @@ extern "C" qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, 
   for (int r = 0; r < n_req; ++r) {
     if (!plans[r] || n_points[r] < 0) return QED_EINVAL;
     if ((plans[r]->prec == QED_MIXED) != mixed) return QED_EINVAL;
-    if (!plans[r]->summed || plans[r]->k > 5) return QED_EUNSUPPORTED;
+    if (!plans[r]->summed || plans[r]->k > 5 || plans[r]->rewrite) return QED_EUNSUPPORTED;
     if (n_points[r] > 0 && (!d_momenta[r] || !d_out[r] || ((uintptr_t)d_momenta[r] & 7u) ||
                             ((uintptr_t)d_out[r] & 7u)))
       return QED_EINVAL;

@@ -14,6 +14,7 @@ struct KernelChoice {
 };
 KernelChoice forward_kernel(int k, bool summed, bool mixed);
 KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
+KernelChoice rewrite_kernel(int k, bool summed, bool mixed);
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
 }  // namespace qed
@@ -43,6 +44,10 @@ struct qed_plan_s {
   int block_adj = 0, grid_adj = 0;
   size_t smem_adj = 0;
   bool has_adj = false;
+  // distributively rewritten DAG (qed_plan_create_rewrite)
+  bool rewrite = false;
+  RwSchedule rsc;
+  SumInstr* d_sinstr = nullptr;
   int device = 0;
   // staging for qed_eval_host
   double* d_stage = nullptr;

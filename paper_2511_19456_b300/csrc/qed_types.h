@@ -64,9 +64,11 @@ struct KParams {
   double* grad;      // adjoint kernel: d|M|^2/dk_j [N][k][3] (may be null otherwise)
   long long n;
   const Instr* instr;
+  const SumInstr* sinstr;   // rewritten-DAG instructions (rewrite plans)
   const Phase* phases;
   const SetEntry* sets;
   int n_stored_phases, n_set_phases, n_sets;
+  int set_group;     // rewrite plans: photon sets per set phase
   int ncur;          // stored + local currents
   int ncur_stored;   // currents kept for the whole point
   int team_bytes;

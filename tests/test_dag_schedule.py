@@ -99,3 +99,47 @@ def test_schedule_interpreter_matches_oracle(orc, k, summed):
         ref = orc.m2(mom, sum_mask=0, hel=hel)
     got = np.array([schedule_interp.evaluate(sched, orc, mom[i], hel) for i in range(len(mom))])
     assert np.allclose(got, ref, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("k,summed,group", [(1, True, 0), (2, True, 0), (3, True, 1), (3, True, 3),
+                                            (4, True, 0), (4, True, 4), (1, False, 0), (2, False, 0),
+                                            (3, False, 0), (5, False, 1), (5, False, 7), (6, False, 0)])
+def test_rewrite_schedule_interpreter_matches_oracle(orc, k, summed, group):
+    """The distributively rewritten DAG (one current per photon subset) gives
+    the same |M|^2 as the brute-force sum over Feynman diagrams, for set groups
+    that divide the photon sets and ones that leave a ragged last group."""
+    sched = schedule_export(k, summed, rewrite=True, group=group)
+    mom = ps.points(k, 3, 1.0 + k, seed=310 + k)
+    if summed:
+        ref = orc.m2(mom)
+        hel = None
+    else:
+        hel = [1, 2, -1] + [1 + (j % 2) for j in range(k)]
+        ref = orc.m2(mom, sum_mask=0, hel=hel)
+    got = np.array([schedule_interp.evaluate_rewrite(sched, orc, mom[i], hel) for i in range(len(mom))])
+    assert np.allclose(got, ref, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("k", range(1, 8))
+def test_rewrite_schedule_structure(k):
+    """One node per (side, subset): left subsets of size 1..h, right subsets of
+    size 1..r; every node sums one term per photon of its subset; one join per
+    photon set of size h."""
+    n = k + 1
+    s = schedule_export(k, True, rewrite=True)
+    h, r = s["h"], s["r"]
+    ins = s["instr"]
+    assert len(s["sets"]) == math.comb(n, h)
+    assert np.all(ins["nterms"] == ins["level"])
+    stored = sum(math.comb(n, l) for l in range(1, h)) + sum(math.comb(n, l) for l in range(1, r))
+    assert s["n_stored_phases"] >= 1 or stored == 0
+    assert len(ins) == stored + 2 * math.comb(n, h)
+    g = s["group"]
+    assert s["local_currents"] == g * ((1 << (h + 1)) + (1 << (r + 1)))
+    assert len(s["phases"]) == s["n_stored_phases"] + -(-math.comb(n, h) // g)
+    ncur = s["stored_currents"] + s["local_currents"]
+    nv = 1 << (ins["level"].astype(int) + 1)
+    assert np.all(ins["dst"] >= 0) and np.all(ins["dst"] + nv <= ncur)
+    for t in range(4):
+        used = ins["nterms"] > t
+        assert np.all(ins["src"][used, t] < ncur)
