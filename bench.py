@@ -41,15 +41,19 @@ PEAK_FP64_TFLOPS = 1.25
 # shape); bumped with every change to it.  DRAM traffic recorded in
 # profiles/traffic.json is reported only for the version it was measured on.
 FWD_KERNEL_VERSION = "fwd-3"
+# The same for the kernel of the distributively rewritten DAG.
+RW_KERNEL_VERSION = "rw-1"
 
 
-def recorded_traffic(workload: str, prec: str, n_points: int):
+def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain"):
+    key = f"{workload}/{prec}" if dag == "plain" else f"{workload}/{dag}/{prec}"
+    version = FWD_KERNEL_VERSION if dag == "plain" else RW_KERNEL_VERSION
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f).get(f"{workload}/{prec}")
+            rec = json.load(f).get(key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("kernel_version") != FWD_KERNEL_VERSION or rec.get("n_points") != n_points:
+    if not rec or rec.get("kernel_version") != version or rec.get("n_points") != n_points:
         return None
     return rec["bytes_per_launch"]
 
@@ -354,6 +358,9 @@ def main():
                     help="time one precision only (profiling runs)")
     ap.add_argument("--n-points", type=int, default=None,
                     help="override the workload's point count (profiling runs)")
+    ap.add_argument("--dag", choices=["plain", "rewrite"], default="plain",
+                    help="plain: the node-reduced DAG (one current per ordered photon prefix); "
+                         "rewrite: the distributively rewritten DAG (one current per photon subset)")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.workload in ("batched", "rewrite_vs_plain"):
@@ -365,7 +372,7 @@ def main():
     if args.workload == "rewrite_vs_plain":
         run_rewrite_compare(args)
         return
-    if args.workload != "compton_k4" and args.only is None:
+    if args.workload != "compton_k4" and args.only is None and args.dag == "plain":
         run_other(args)
         return
 
@@ -398,7 +405,7 @@ def main():
     if args.only:
         legs = [l for l in legs if l[0] == args.only]
     for prec, steps in legs:
-        plan = Plan(k, summed=w["summed"], hel=hel, precision=prec)
+        plan = Plan(k, summed=w["summed"], hel=hel, precision=prec, rewrite=args.dag == "rewrite")
         info = plan.info()
         with ClockSampler(local) as cs:
             ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier)
@@ -411,7 +418,7 @@ def main():
         res[prec] = {"value": pts, "ms_per_step": ms, "plan": plan, "info": info,
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                                   "unit": "TFLOP/s", "frac": achieved / peak,
-                                  "traffic": recorded_traffic(args.workload, prec, n),
+                                  "traffic": recorded_traffic(args.workload, prec, n, args.dag),
                                   "peak_source": "derived from unit counts and the 2032 MHz clock"
                                   if prec == "mixed" else "nominal B300 FP64 rate",
                                   "pipe": "FP32 FMA" if prec == "mixed" else "FP64 FMA",
@@ -424,7 +431,8 @@ def main():
         # profiling run: one precision, no end-to-end leg, a short line
         r = res[args.only]
         if rank == 0:
-            print(json.dumps({"profile_run": args.only, "workload": args.workload, "n_points": n,
+            print(json.dumps({"profile_run": args.only, "workload": args.workload, "dag": args.dag,
+                              "n_points": n,
                               "ms_per_step": r["ms_per_step"], "value": r["value"],
                               "roofline": r["roofline"]}), flush=True)
         if ws > 1:
@@ -472,7 +480,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "k": k, "n_points": n, "omega": w["omega"],
+        "config": {"workload": args.workload, "dag": args.dag, "k": k, "n_points": n, "omega": w["omega"],
                    "states_summed": mixed["info"]["n_states"], "diagrams": mixed["info"]["n_diagrams"],
                    "generator": "RAMBO (seeded SplitMix64)" if k > 1 else "flat 2-body",
                    "l2": f"inputs {n * (k + 3) * 32 / 1e6:.0f} MB per step, larger than the 126 MB L2",

@@ -41,6 +41,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_phases_adj);
   cudaFree(p->d_sets_adj);
   cudaFree(p->d_sinstr);
+  cudaFree(p->d_lane_tab);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
@@ -67,6 +68,7 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.n = n;
   kp.instr = P->d_instr;
   kp.sinstr = P->d_sinstr;
+  kp.lane_tab = P->d_lane_tab;
   kp.phases = P->d_phases;
   kp.sets = P->d_sets;
   if (P->rewrite) {
@@ -266,6 +268,24 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
     return QED_EUNSUPPORTED;
   }
   if (rewrite) {
+    if (P->summed) {
+      const int n = k + 1;
+      std::vector<uint16_t> tab(P->rsc.sets.size() << n);
+      for (size_t s = 0; s < P->rsc.sets.size(); ++s) {
+        const unsigned S = P->rsc.sets[s].mask, C = ((1u << n) - 1) & ~S;
+        for (unsigned c = 0; c < (1u << n); ++c) {
+          unsigned l = 0, r = 0;
+          int ol = 0, orr = 0;
+          for (int j = 0; j < n; ++j) {
+            const unsigned b = (c >> j) & 1u;
+            if (S & (1u << j)) l |= b << ol++;
+            if (C & (1u << j)) r |= b << orr++;
+          }
+          tab[(s << n) + c] = (uint16_t)(l | (r << 8));
+        }
+      }
+      if (e == cudaSuccess) e = upload(&P->d_lane_tab, tab);
+    }
     if (e == cudaSuccess) e = upload(&P->d_sinstr, P->rsc.instr);
     if (e == cudaSuccess) e = upload(&P->d_phases, P->rsc.phases);
     if (e == cudaSuccess) e = upload(&P->d_sets, P->rsc.sets);

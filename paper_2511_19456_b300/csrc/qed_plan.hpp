@@ -48,6 +48,7 @@ struct qed_plan_s {
   bool rewrite = false;
   RwSchedule rsc;
   SumInstr* d_sinstr = nullptr;
+  uint16_t* d_lane_tab = nullptr;   // spin-summed rewrite plans: leaf variants per (set, lane)
   int device = 0;
   // staging for qed_eval_host
   double* d_stage = nullptr;

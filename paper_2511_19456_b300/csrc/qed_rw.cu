@@ -24,13 +24,55 @@ __device__ __forceinline__ SumInstr ld_sum_instr(const SumInstr* p) {
   return in;
 }
 
-template <bool SUMMED, typename Real>
+// y += SIGN (sigma . a) x, column and row forms (SIGN = +-1), as FMA chains.
+template <int SIGN, typename R>
+__device__ __forceinline__ void pauli_col_acc(const R a[3], const R x[4], R y[4]) {
+  const R ax = SIGN * a[0], ay = SIGN * a[1], az = SIGN * a[2];
+  y[0] = fma(az, x[0], fma(ax, x[2], fma(ay, x[3], y[0])));
+  y[1] = fma(az, x[1], fma(ax, x[3], fma(-ay, x[2], y[1])));
+  y[2] = fma(ax, x[0], fma(-ay, x[1], fma(-az, x[2], y[2])));
+  y[3] = fma(ax, x[1], fma(ay, x[0], fma(-az, x[3], y[3])));
+}
+template <int SIGN, typename R>
+__device__ __forceinline__ void pauli_row_acc(const R a[3], const R x[4], R y[4]) {
+  const R ax = SIGN * a[0], ay = SIGN * a[1], az = SIGN * a[2];
+  y[0] = fma(az, x[0], fma(ax, x[2], fma(-ay, x[3], y[0])));
+  y[1] = fma(az, x[1], fma(ax, x[3], fma(ay, x[2], y[1])));
+  y[2] = fma(ax, x[0], fma(ay, x[1], fma(-az, x[2], y[2])));
+  y[3] = fma(ax, x[1], fma(-ay, x[0], fma(-az, x[3], y[3])));
+}
+
+// acc += eps/ x (side 0, column) or x eps/ (side 1, row); eps/ as in vertex_col/row.
+template <typename R>
+__device__ __forceinline__ void vertex_acc(int side, const R e[3], const R x[8], R acc[8]) {
+  if (side == 0) {
+    pauli_col_acc<-1>(e, x + 4, acc);
+    pauli_col_acc<1>(e, x, acc + 4);
+  } else {
+    pauli_row_acc<1>(e, x + 4, acc);
+    pauli_row_acc<-1>(e, x, acc + 4);
+  }
+}
+
+__device__ __forceinline__ void load_eps(const float* p, float e[3]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  e[0] = v.x; e[1] = v.y; e[2] = v.z;
+}
+__device__ __forceinline__ void load_eps(const double* p, double e[3]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  e[0] = v.x; e[1] = v.y; e[2] = p[2];
+}
+
+// One node of the rewritten DAG, variant v: the sum of its NT vertex terms,
+// then the propagator of its post set.
+template <int NT, bool SUMMED, typename Real>
 __device__ __forceinline__ void apply_sum(const SumInstr& in, int v, const KParams& p, const Real* s_q,
                                           const Real* s_eps, const Real* s_spin, Real* s_cur) {
   Real acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = (Real)0;
-  for (int t = 0; t < in.nterms; ++t) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
     const int j = in.photon[t];
     int pol, vp;
     if constexpr (SUMMED) {
@@ -41,18 +83,16 @@ __device__ __forceinline__ void apply_sum(const SumInstr& in, int v, const KPara
       pol = (int)((p.fixed_pol_bits >> j) & 1u);
       vp = 0;
     }
-    Real x[8], y[8];
+    Real x[8];
     if (in.src[t] < 0) {
       const int e = SUMMED ? vp : (in.side == 0 ? p.fixed_sin : p.fixed_sout);
       load8(s_spin + (in.side * 2 + e) * 8, x);
     } else {
       load_cur(s_cur, in.src[t], 0, vp, x);
     }
-    const Real* e3 = s_eps + (j * 2 + pol) * 4;
-    const Real ev[3] = {e3[0], e3[1], e3[2]};
-    if (in.side == 0) vertex_col(ev, x, y); else vertex_row(ev, x, y);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] += y[c];
+    Real ev[3];
+    load_eps(s_eps + (j * 2 + pol) * 4, ev);
+    vertex_acc(in.side, ev, x, acc);
   }
   if (in.post) {
     const Real* P = s_q + in.post * 5;
@@ -64,6 +104,18 @@ __device__ __forceinline__ void apply_sum(const SumInstr& in, int v, const KPara
   }
 }
 
+template <int NT, int TEAM, bool SUMMED, typename Real>
+__device__ __forceinline__ void run_slot(int beg, int cnt, int lg, int lane, const KParams& p, const Real* s_q,
+                                         const Real* s_eps, const Real* s_spin, Real* s_cur) {
+  const int total = cnt << lg;
+  for (int it = lane; it < total; it += TEAM) {
+    const SumInstr in = ld_sum_instr(p.sinstr + beg + (it >> lg));
+    apply_sum<NT, SUMMED, Real>(in, it & ((1 << lg) - 1), p, s_q, s_eps, s_spin, s_cur);
+  }
+}
+
+// A phase: up to two ranges of nodes of one level each (every node of a
+// level sums as many terms as the level).
 template <int TEAM, bool SUMMED, typename Real>
 __device__ __forceinline__ void run_sum_phase(const Phase& ph, int lane, const KParams& p, const Real* s_q,
                                               const Real* s_eps, const Real* s_spin, Real* s_cur) {
@@ -71,19 +123,31 @@ __device__ __forceinline__ void run_sum_phase(const Phase& ph, int lane, const K
   for (int slot = 0; slot < 2; ++slot) {
     const int cnt = ph.cnt[slot];
     if (cnt == 0) continue;
-    const int lg = SUMMED ? ph.level[slot] + 1 : 0;
-    const int total = cnt << lg;
-    for (int it = lane; it < total; it += TEAM) {
-      const SumInstr in = ld_sum_instr(p.sinstr + ph.beg[slot] + (it >> lg));
-      apply_sum<SUMMED, Real>(in, it & ((1 << lg) - 1), p, s_q, s_eps, s_spin, s_cur);
+    const int lev = ph.level[slot];
+    const int lg = SUMMED ? lev + 1 : 0;
+    switch (lev) {
+      case 1: run_slot<1, TEAM, SUMMED, Real>(ph.beg[slot], cnt, lg, lane, p, s_q, s_eps, s_spin, s_cur); break;
+      case 2: run_slot<2, TEAM, SUMMED, Real>(ph.beg[slot], cnt, lg, lane, p, s_q, s_eps, s_spin, s_cur); break;
+      case 3: run_slot<3, TEAM, SUMMED, Real>(ph.beg[slot], cnt, lg, lane, p, s_q, s_eps, s_spin, s_cur); break;
+      default: run_slot<4, TEAM, SUMMED, Real>(ph.beg[slot], cnt, lg, lane, p, s_q, s_eps, s_spin, s_cur); break;
     }
   }
 }
 
 }  // namespace
 
+// Block: one team when TEAM > 32, else 128 threads; FP64 instances may use up
+// to about 96 registers per thread, FP32 ones 64.
+template <typename Real, int TEAM>
+constexpr int rw_block() { return TEAM > 32 ? TEAM : 128; }
+template <typename Real, int TEAM>
+constexpr int rw_min_blocks() {
+  constexpr int b = 65536 / (rw_block<Real, TEAM>() * (sizeof(Real) == 8 ? 96 : 64));
+  return b < 1 ? 1 : b;
+}
+
 template <int K, bool SUMMED, typename Real, int TEAM>
-__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256)
+__global__ void __launch_bounds__(rw_block<Real, TEAM>(), rw_min_blocks<Real, TEAM>())
 qed_rw_kernel(const KParams p) {
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;
@@ -123,11 +187,19 @@ qed_rw_kernel(const KParams p) {
       run_sum_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + gi), lane, p, s_q, s_eps, s_spin, s_cur);
       team_sync<TEAM>();
       if constexpr (SUMMED) {
+        // state (si, so, c) of lane c: left variant pext(c, S), right
+        // variant pext(c, not S), from the plan's lane table
         const unsigned c = (unsigned)lane & ALL;
+        Real yr[4], yi[4];
+        if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i].start(yr[i], yi[i]);
+        }
         for (int s = g0; s < g1; ++s) {
           const SetEntry se = p.sets[s];
-          const int vl = (int)pext_bits(c, se.mask, N) << 1;
-          const int vr = (int)pext_bits(c, ALL & ~se.mask, N) << 1;
+          const unsigned tv = __ldg(p.lane_tab + (s << N) + c);
+          const int vl = (int)(tv & 0xffu) << 1;
+          const int vr = (int)(tv >> 8) << 1;
           Real lc[2][8], rw[2][8];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
@@ -138,15 +210,14 @@ qed_rw_kernel(const KParams p) {
           for (int si = 0; si < 2; ++si)
 #pragma unroll
             for (int so = 0; so < 2; ++so) {
-              if constexpr (sizeof(Real) == 8) {
-                dot_acc(rw[so], lc[si], acc[si * 2 + so].re, acc[si * 2 + so].im);
-              } else {
-                float yr, yi;
-                acc[si * 2 + so].start(yr, yi);
-                dot_acc(rw[so], lc[si], yr, yi);
-                acc[si * 2 + so].commit(yr, yi);
-              }
+              if constexpr (sizeof(Real) == 8) dot_acc(rw[so], lc[si], acc[si * 2 + so].re, acc[si * 2 + so].im);
+              else dot_acc(rw[so], lc[si], yr[si * 2 + so], yi[si * 2 + so]);
             }
+        }
+        // the group's joins are one compensated step
+        if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i].commit(yr[i], yi[i]);
         }
       } else {
         // one fixed state: the lanes take the group's joins

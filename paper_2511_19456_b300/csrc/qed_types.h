@@ -69,6 +69,10 @@ struct KParams {
   const SetEntry* sets;
   int n_stored_phases, n_set_phases, n_sets;
   int set_group;     // rewrite plans: photon sets per set phase
+  // rewrite plans, spin-summed: for set s and photon-polarisation pattern c,
+  // entry [s][c] = pext(c, S) | pext(c, not S) << 8 (left and right leaf
+  // variant without the helicity bit)
+  const uint16_t* lane_tab;
   int ncur;          // stored + local currents
   int ncur_stored;   // currents kept for the whole point
   int team_bytes;
