@@ -40,9 +40,9 @@ PEAK_FP64_TFLOPS = 1.25
 # Version of the forward kernel (arithmetic, shared-memory layout, launch
 # shape); bumped with every change to it.  DRAM traffic recorded in
 # profiles/traffic.json is reported only for the version it was measured on.
-FWD_KERNEL_VERSION = "fwd-3"
+FWD_KERNEL_VERSION = "fwd-4"
 # The same for the kernel of the distributively rewritten DAG.
-RW_KERNEL_VERSION = "rw-1"
+RW_KERNEL_VERSION = "rw-2"
 
 
 def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain"):

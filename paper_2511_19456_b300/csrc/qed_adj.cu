@@ -272,7 +272,8 @@ qed_adj_kernel(const KParams p) {
     const long long ptc = valid ? pt : p.n - 1;
 
     // ---- 1. forward pass
-    point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin);
+    point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin,
+                               reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
     for (int ph = 0; ph < p.n_stored_phases; ++ph) {
       run_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur);
       team_sync<TEAM>();

@@ -175,7 +175,8 @@ qed_rw_kernel(const KParams p) {
   for (long long pt0 = (long long)blockIdx.x * tpc; pt0 < p.n; pt0 += (long long)gridDim.x * tpc) {
     const long long pt = pt0 + team;
     const bool valid = pt < p.n;
-    point_setup<K, Real, TEAM>(p, lane, valid ? pt : p.n - 1, s_mom, s_q, s_eps, s_spin);
+    point_setup<K, Real, TEAM>(p, lane, valid ? pt : p.n - 1, s_mom, s_q, s_eps, s_spin,
+                               reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
     for (int ph = 0; ph < p.n_stored_phases; ++ph) {
       run_sum_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur);
       team_sync<TEAM>();

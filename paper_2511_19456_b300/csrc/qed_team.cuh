@@ -184,32 +184,132 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double vim() const { return (double)im - (double)cim; }
 };
 
+// Minkowski product in FP64.
+__device__ __forceinline__ double mdot(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(-a[1], b[1], fma(-a[2], b[2], -a[3] * b[3])));
+}
+
 // Per point: momenta into shared memory, the propagator table (a3) and the
 // external states (a2).
+//
+// FP64 form: Q_T = p + sum_{j in T} sigma_j k_j (sigma = +1 for the incoming
+// photon, -1 for the outgoing ones) and D_T = Q_T^2 - m^2, both in FP64.
+//
+// Mixed form: the same D_T, in FP64, but summed from Lorentz invariants
+// computed once per point,
+//   D_T = (p^2 - m^2) + sum_{j in T} (k_j^2 + 2 sigma_j p.k_j)
+//         + sum_{i<j in T} 2 sigma_i sigma_j k_i.k_j,
+// or, for |T| > n/2, from the outgoing electron's side with the complement,
+//   Q_T = p' - sum_{j not in T} sigma_j k_j,
+// so that no denominator sums more than n/2 photons.  Q_T itself, which only
+// enters the FP32 numerator, is summed in float-float arithmetic on the FP32
+// pipe (Knuth's TwoSum on the high parts, the low parts added) and rounded
+// once, as accurate as rounding an FP64 sum.  This keeps the FP64 pipe (1/64
+// of the FP32 rate) off the critical path where a thread builds several
+// subsets or subsets of many photons (n >= 7); with one subset of few photons
+// per thread the FP64 form is as fast, and it is used there.
 template <int K, typename Real, int TEAM>
 __device__ __forceinline__ void point_setup(const KParams& p, int lane, long long ptc, double* s_mom,
-                                          Real* s_q, Real* s_eps, Real* s_spin) {
+                                          Real* s_q, Real* s_eps, Real* s_spin, double* s_w,
+                                          float* s_momf) {
   constexpr int N = K + 1;
   constexpr int NS = K + 3;
   constexpr int NSUB = 1 << N;
   constexpr unsigned ALL = (1u << N) - 1;
+  constexpr bool INV = sizeof(Real) == 4 && (NSUB > TEAM || N >= 7);
   // ---- a1: load the point
-  for (int i = lane; i < NS * 4; i += TEAM) s_mom[i] = __ldg(p.mom + ptc * (NS * 4) + i);
+  for (int i = lane; i < NS * 4; i += TEAM) {
+    const double v = __ldg(p.mom + ptc * (NS * 4) + i);
+    s_mom[i] = v;
+    if constexpr (INV) {
+      const float hi = (float)v;
+      s_momf[i] = hi;                          // v = hi + lo to about 2^-48
+      s_momf[NS * 4 + i] = (float)(v - (double)hi);
+    }
+  }
   team_sync<TEAM>();
 
-  // ---- a3: propagator entries of every photon subset, one subset per
-  // thread (momenta and denominators in FP64)
-  for (int mask = lane; mask < NSUB; mask += TEAM) {
-    Real* d = s_q + mask * 5;
-    Real P[5];
-    if (mask == 0 || mask == (int)ALL) {
+  if constexpr (!INV) {
+    // ---- a3: propagator entries of every photon subset, one subset per
+    // thread (momenta and denominators in FP64)
+    for (int mask = lane; mask < NSUB; mask += TEAM) {
+      Real* d = s_q + mask * 5;
+      Real P[5];
+      if (mask == 0 || mask == (int)ALL) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) P[c] = (Real)0;
-    } else {
-      make_prop<Real>(s_mom, N, (unsigned)mask, p.mass, P);
+        for (int c = 0; c < 5; ++c) P[c] = (Real)0;
+      } else {
+        make_prop<Real>(s_mom, N, (unsigned)mask, p.mass, P);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d[c] = P[c];
     }
+  } else {
+    // ---- a3, mixed: the invariants [p^2-m^2, p'^2-m^2, in-side singles,
+    // out-side singles, pairs (N x N, i < j used)]
+    constexpr int NPAIR = N * (N - 1) / 2;
+    const double* pin = s_mom;
+    const double* pout = s_mom + 8;
+    for (int it = lane; it < 2 + 2 * N + NPAIR; it += TEAM) {
+      if (it < 2) {
+        const double* q = it == 0 ? pin : pout;
+        s_w[it] = fma(-p.mass, p.mass, mdot(q, q));
+      } else if (it < 2 + 2 * N) {
+        const int j = (it - 2) % N;
+        const bool out = it >= 2 + N;
+        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
+        const double two_sigma = (j == 0) != out ? 2.0 : -2.0;   // in: 2 sigma_j; out: -2 sigma_j
+        s_w[it] = fma(two_sigma, mdot(out ? pout : pin, kj), mdot(kj, kj));
+      } else {
+        int r = it - 2 - 2 * N, i = 0;
+        while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
+        const int j = i + 1 + r;
+        const double* ki = s_mom + 4 * (i == 0 ? 1 : i + 2);
+        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
+        const double two_ss = i == 0 ? -2.0 : 2.0;   // 2 sigma_i sigma_j (j >= 1)
+        s_w[2 + 2 * N + i * N + j] = two_ss * mdot(ki, kj);
+      }
+    }
+    team_sync<TEAM>();
+    for (int mask = lane; mask < NSUB; mask += TEAM) {
+      float* d = reinterpret_cast<float*>(s_q) + mask * 5;
+      if (mask == 0 || mask == (int)ALL) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) d[c] = P[c];
+        for (int c = 0; c < 5; ++c) d[c] = 0.f;
+        continue;
+      }
+      const bool out = 2 * __popc(mask) > N;
+      const unsigned U = out ? ALL & ~(unsigned)mask : (unsigned)mask;
+      double D = s_w[out ? 1 : 0];
+      float qh[4], ql[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        qh[c] = s_momf[(out ? 8 : 0) + c];
+        ql[c] = s_momf[NS * 4 + (out ? 8 : 0) + c];
+      }
+      for (unsigned a = U; a; a &= a - 1) {
+        const int j = __ffs(a) - 1;
+        D += s_w[2 + (out ? N : 0) + j];
+        for (unsigned b = a & (a - 1); b; b &= b - 1) D += s_w[2 + 2 * N + j * N + (__ffs(b) - 1)];
+        const int o = 4 * (j == 0 ? 1 : j + 2);
+        const float sg = (j == 0) != out ? 1.f : -1.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float sum, err;
+          two_sum_f(qh[c], sg * s_momf[o + c], sum, err);
+          qh[c] = sum;
+          ql[c] = __fadd_rn(ql[c], __fadd_rn(err, sg * s_momf[NS * 4 + o + c]));
+        }
+      }
+      const float inv = 1.0f / (float)D;
+      const float m = (float)p.mass;
+      // Q0 -+ m: the high part first (exact where Q0 is close to m)
+      d[0] = __fadd_rn(__fadd_rn(qh[0], m), ql[0]) * inv;
+      d[1] = __fadd_rn(__fsub_rn(qh[0], m), ql[0]) * inv;
+      d[2] = __fadd_rn(qh[1], ql[1]) * inv;
+      d[3] = __fadd_rn(qh[2], ql[2]) * inv;
+      d[4] = __fadd_rn(qh[3], ql[3]) * inv;
+    }
   }
   // ---- a2: external states u(p, +-), ubar(p', +-), eps_j(pol 1, 2) in
   // the working precision
@@ -228,7 +328,6 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
     }
   }
   team_sync<TEAM>();
-
 }
 
 // The S2 joins of every diagram whose left photon set is se.mask (a6), summed

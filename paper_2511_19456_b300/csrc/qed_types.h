@@ -15,8 +15,13 @@ namespace qed {
 
 // Shared-memory layout of one team (the threads that evaluate one point).
 struct TeamLayout {
-  int mom, q, eps, spin, red, cur, bytes;
+  int mom, q, eps, spin, red, w, momf, cur, bytes;
 };
+
+// Mixed form's set-up scratch: FP64 Lorentz invariants from which every
+// denominator is summed (see point_setup), and the momenta as float-float
+// pairs.
+QED_HD int n_invariants(int n) { return 2 + 2 * n + n * n; }
 
 QED_HD int align16(int x) { return (x + 15) & ~15; }
 
@@ -30,7 +35,14 @@ QED_HD TeamLayout team_layout(int k, int real_size, int ncur) {
   L.eps = off;  off = align16(off + n * 2 * 4 * real_size);
   L.spin = off; off = align16(off + 2 * 2 * 8 * real_size);
   L.red = off;  off = align16(off + 16 * 8);
-  L.cur = off;  off = align16(off + ncur * 8 * real_size);
+  // the currents; the mixed form's set-up scratch (invariants, float-float
+  // momenta) shares their space, as it is dead before the first current
+  L.cur = off;
+  const int cur_bytes = ncur * 8 * real_size;
+  const int scratch = real_size == 4 ? align16(n_invariants(n) * 8) + (k + 3) * 4 * 4 * 2 : 0;
+  L.w = off;
+  L.momf = off + align16(n_invariants(n) * 8);
+  off = align16(off + (cur_bytes > scratch ? cur_bytes : scratch));
   L.bytes = off;
   return L;
 }
