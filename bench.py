@@ -321,6 +321,47 @@ def run_rewrite_compare(args):
     print(json.dumps(res), flush=True)
 
 
+def run_abc(args):
+    """The ABC model (paper App. F) through the same DAGs as QED with one spin
+    state: points/s and FLOP rates of the node-reduced and the rewritten DAG,
+    FP64 and mixed, for k = 1, 3, 5, 7, next to QED with one fixed state on
+    the same k (the same DAG with 4x4 Dirac building blocks)."""
+    import torch
+    from paper_2511_19456_b300 import AbcPlan, Plan
+    torch.cuda.set_device(0)
+    res = {"workload": "abc", "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+           "metric": METRIC, "unit": "points/s", "masses": ps.ABC_MASSES}
+    fixed_hel = {1: [1, 2, -1, 1], 3: [1, 2, -1, 1, 2, 1], 5: [1, 2, -1] + [1, 2] * 2 + [1],
+                 7: [1, 2, -1] + [1, 2] * 3 + [1]}
+    for name, w in ps.ABC_WORKLOADS.items():
+        k, n = w["k"], w["n_points"]
+        mom = torch.from_numpy(ps.abc_workload_points(name)).cuda()
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        legs = {"n_points": n, "rs": w["rs"]}
+        for dag in ("plain", "rewrite"):
+            for prec in ("fp64", "mixed"):
+                plan = AbcPlan(k, precision=prec, rewrite=dag == "rewrite", **ps.ABC_MASSES)
+                ms = time_calls(lambda: plan.eval(mom, out), args.steps, args.warmup)
+                fl = plan.info()["flops_per_point"]
+                peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+                legs[f"{dag}_{prec}"] = {"points_per_s": n / (ms * 1e-3), "ms": ms, "flops_per_point": fl,
+                                         "tflops": fl * n / (ms * 1e-3) / 1e12,
+                                         "frac_of_peak": fl * n / (ms * 1e-3) / 1e12 / peak}
+        # QED, one fixed state, same k and DAG structure, QED kinematics
+        qmom = torch.from_numpy(ps.points(k, n, 2.0 * k, w["seed"])).cuda()
+        for prec in ("fp64", "mixed"):
+            qp = Plan(k, summed=False, hel=fixed_hel[k], precision=prec)
+            ms = time_calls(lambda: qp.eval(qmom, out), args.steps, args.warmup)
+            legs[f"qed_fixed_plain_{prec}"] = {"points_per_s": n / (ms * 1e-3), "ms": ms,
+                                               "flops_per_point": qp.info()["flops_per_point"]}
+        legs["abc_over_qed_points_per_s_plain_fp64"] = (legs["plain_fp64"]["points_per_s"]
+                                                       / legs["qed_fixed_plain_fp64"]["points_per_s"])
+        res[name] = legs
+    res["value"] = res["abc_k7"]["plain_fp64"]["points_per_s"]
+    res["config"] = {"workload": "abc", "k": "1, 3, 5, 7", "dag": "plain and rewrite"}
+    print(json.dumps(res), flush=True)
+
+
 def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     import torch
     for _ in range(warmup):
@@ -345,7 +386,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched", "rewrite_vs_plain"],
+    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched", "rewrite_vs_plain", "abc"],
                     help="compton_k4 is the headline line; the others measure the other "
                          "configurations (adjoint at k = 6, k = 7, the batched stream)")
     ap.add_argument("--fp64-steps", type=int, default=None,
@@ -363,7 +404,7 @@ def main():
                          "rewrite: the distributively rewritten DAG (one current per photon subset)")
     args = ap.parse_args()
     if args.impl == "reference":
-        if args.workload in ("batched", "rewrite_vs_plain"):
+        if args.workload in ("batched", "rewrite_vs_plain", "abc"):
             print(json.dumps({"impl": "reference", "unavailable":
                               "the batched stream is measured against the FP64 GPU path"}))
             return
@@ -371,6 +412,9 @@ def main():
         return
     if args.workload == "rewrite_vs_plain":
         run_rewrite_compare(args)
+        return
+    if args.workload == "abc":
+        run_abc(args)
         return
     if args.workload != "compton_k4" and args.only is None and args.dag == "plain":
         run_other(args)

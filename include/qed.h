@@ -132,6 +132,41 @@ qed_status qed_plan_create(const qed_process* process, const qed_spin_cfg* spin,
 qed_status qed_plan_create_rewrite(const qed_process* process, const qed_spin_cfg* spin,
                                    qed_precision precision, qed_plan_t* out);
 
+/* The ABC model (paper App. F and Sec. I-C). It has three scalar particles
+ * A, B and C and one vertex joining one of each.
+ *
+ * Process: A(p) B(k_0) -> A(p') B(k_1) ... B(k_k), with the momenta laid out
+ * as for QED (slot 0 = A in, 1 = B in, 2 = A out, 3.. = B out).
+ *
+ * The B lines attach in all n! = (k+1)! orders to the A/C line, whose
+ * species alternates at each attachment: C after an odd number, A after an
+ * even number. Hence
+ *   |M|^2 = g^(2n) [sum_orders prod_{i<n} 1/(Q_i^2 - m_{s(i)}^2)]^2.
+ * For an odd n (even k) no diagram exists.
+ *
+ * Fields:
+ *   k: odd, in {1, 3, 5, 7};
+ *   mass_a, mass_c: A and C masses (>= 0);
+ *   mass_b: the B mass, which enters only through the caller's momenta;
+ *   coupling: g. */
+typedef struct {
+  int k;
+  double mass_a, mass_b, mass_c;
+  double coupling;
+} qed_abc_process;
+
+/* Plan for the ABC model through the same node-reduced DAG as QED with one
+ * spin state (rewrite = 0), or through the rewritten DAG (rewrite != 0),
+ * with scalar currents. The kernels are in csrc/abc_kernel.cu.
+ *
+ * Accepted: qed_eval, qed_eval_host, qed_plan_info, qed_plan_destroy. The
+ * FLOPs are those of the scalar DAG.
+ * Returns QED_EUNSUPPORTED: qed_eval_grad and the batched entry points.
+ * Returns QED_EINVAL: NULL pointers, an even or out-of-range k, a negative or
+ * non-finite mass, a non-finite coupling. */
+qed_status qed_abc_plan_create(const qed_abc_process* process, qed_precision precision, int rewrite,
+                               qed_plan_t* out);
+
 qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 
 /* out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4

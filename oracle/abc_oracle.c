@@ -65,11 +65,15 @@ static double one_point(int k, const double* mom, double ma, double mc, double* 
   }
   double sum = 0.0, comp = 0.0, abs_sum = 0.0;
   do {
-    double q[4] = {mom[0], mom[1], mom[2], mom[3]};
     double amp = 1.0;
+    unsigned attached = 0;
     for (int i = 1; i < n; ++i) {
-      const int j = order[i - 1];
-      for (int c = 0; c < 4; ++c) q[c] += sign[j] * kb[j][c];
+      attached |= 1u << order[i - 1];
+      /* Q_i from scratch: p, then the attached B's in ascending slot order */
+      double q[4] = {mom[0], mom[1], mom[2], mom[3]};
+      for (int j = 0; j < n; ++j)
+        if (attached & (1u << j))
+          for (int c = 0; c < 4; ++c) q[c] += sign[j] * kb[j][c];
       const double m = (i % 2 == 1) ? mc : ma;
       amp /= mdot(q, q) - m * m;
     }

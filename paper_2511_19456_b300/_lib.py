@@ -26,6 +26,11 @@ class Process(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("mass", ctypes.c_double), ("charge", ctypes.c_double)]
 
 
+class AbcProcess(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("mass_a", ctypes.c_double), ("mass_b", ctypes.c_double),
+                ("mass_c", ctypes.c_double), ("coupling", ctypes.c_double)]
+
+
 class SpinCfg(ctypes.Structure):
     _fields_ = [("summed", ctypes.c_int), ("hel", ctypes.c_byte * 10)]
 
@@ -66,6 +71,8 @@ SIGNATURES = [
                                        ctypes.c_int, ctypes.POINTER(_vp)]),
     ("qed_plan_create_rewrite", ctypes.c_int, [ctypes.POINTER(Process), ctypes.POINTER(SpinCfg),
                                                ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("qed_abc_plan_create", ctypes.c_int, [ctypes.POINTER(AbcProcess), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(_vp)]),
     ("qed_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
     ("qed_eval", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),
     ("qed_eval_grad", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, _vp]),

@@ -132,6 +132,31 @@ class Plan:
             pass
 
 
+class AbcPlan(Plan):
+    """A plan for the ABC model (paper App. F): A B -> A + k B, k odd in
+    1..7, through the node-reduced DAG (rewrite=False) or the rewritten DAG,
+    with scalar currents.  Momenta as for QED (slot 0 A in, 1 B in, 2 A out,
+    3.. B out).  mass_b enters only through the momenta."""
+
+    def __init__(self, k: int, precision: str = "fp64", rewrite: bool = False, mass_a: float = 1.0,
+                 mass_b: float = 0.0, mass_c: float = 1.0, coupling: float = 1.0):
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {sorted(_PREC)}")
+        proc = _lib.AbcProcess(int(k), float(mass_a), float(mass_b), float(mass_c), float(coupling))
+        handle = ctypes.c_void_p()
+        check(_lib.lib().qed_abc_plan_create(ctypes.byref(proc), _PREC[precision], 1 if rewrite else 0,
+                                             ctypes.byref(handle)), "qed_abc_plan_create")
+        self._h = handle
+        self.rewrite = bool(rewrite)
+        self.k = int(k)
+        self.summed = False
+        self.hel = None
+        self.precision = precision
+        self.mass = float(mass_a)
+        self.mass_c = float(mass_c)
+        self.coupling = float(coupling)
+
+
 def dag_counts(k: int) -> dict:
     """Node counts of the per-diagram CDAG and of its node-reduced form."""
     c = _lib.DagCounts()

@@ -162,5 +162,9 @@ constexpr int FLOP_SUBSET = 20; // Q_S, D_S = Q^2 - m^2, 1/D and scaled entries
 constexpr int FLOP_SQUARE = 4;  // |M|^2 of one state added to the spin sum
 constexpr int FLOP_SPINOR = 30;
 constexpr int FLOP_POL = 15;
+// ABC model (scalar currents; the vertex factor g is applied once as g^(2n))
+constexpr int FLOP_ABC_SUBSET = 9;  // Q_S^2 - m^2 (4 mul, 4 sub) and 1/D
+constexpr int FLOP_ABC_S1 = 1;      // current times 1/D
+constexpr int FLOP_ABC_JOIN = 2;    // product of two leaves added to M
 
 }  // namespace qed

@@ -88,6 +88,7 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   }
   kp.team_bytes = P->team_bytes;
   kp.mass = P->mass;
+  kp.mass_c = P->mass_c;
   kp.coupling = std::pow(P->charge, 2.0 * (P->k + 1));
   kp.fixed_sin = P->fixed_sin;
   kp.fixed_sout = P->fixed_sout;
@@ -333,6 +334,89 @@ qed_status qed_plan_create_rewrite(const qed_process* process, const qed_spin_cf
   return create_plan(process, spin, precision, true, out);
 }
 
+qed_status qed_abc_plan_create(const qed_abc_process* proc, qed_precision precision, int rewrite,
+                               qed_plan_t* out) {
+  if (!proc || !out) return QED_EINVAL;
+  const int k = proc->k;
+  if (k < 1 || k > 7 || k % 2 == 0) return QED_EINVAL;
+  for (double m : {proc->mass_a, proc->mass_b, proc->mass_c})
+    if (!(m >= 0.0) || !std::isfinite(m)) return QED_EINVAL;
+  if (!std::isfinite(proc->coupling)) return QED_EINVAL;
+  if (precision != QED_FP64 && precision != QED_MIXED) return QED_EINVAL;
+  const bool mixed = precision == QED_MIXED;
+  qed_plan_s* P = new (std::nothrow) qed_plan_s();
+  if (!P) return QED_ENOMEM;
+  P->k = k;
+  P->summed = false;
+  P->prec = precision;
+  P->mass = proc->mass_a;
+  P->mass_c = proc->mass_c;
+  P->charge = proc->coupling;
+  P->abc = true;
+  P->rewrite = rewrite != 0;
+  P->kc = abc_kernel_for(k, mixed, P->rewrite);
+  if (!P->kc.fn) { delete P; return QED_EUNSUPPORTED; }
+  int dev_smem = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e != cudaSuccess) { delete P; return cuda_status(e); }
+  const int n = k + 1;
+  try {
+    int ls, rs;
+    default_levels(k, false, &ls, &rs);
+    P->sc = build_schedule(k, false, ls, rs);
+    if (P->rewrite) P->rsc = build_rewrite_schedule(k, false, rewrite_default_group(k, false, P->kc.team));
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return QED_ENOMEM;
+  } catch (...) {
+    delete P;
+    return QED_EUNSUPPORTED;
+  }
+  // algorithmic FLOPs of the scalar DAG, each node once
+  long long fl = ((1ll << n) - 2) * FLOP_ABC_SUBSET + 2;
+  if (P->rewrite) {
+    fl += (P->rsc.terms - P->rsc.nodes) + P->rsc.s1_nodes * FLOP_ABC_S1 + P->rsc.joins * FLOP_ABC_JOIN;
+  } else {
+    long long right_leaves = 0, fr = 1, c = 1;
+    for (int i = 2; i <= P->sc.r; ++i) fr *= i;
+    for (int i = 1; i <= P->sc.h; ++i) c = c * (n - P->sc.h + i) / i;
+    right_leaves = c * fr;   // the middle propagator, applied to each right leaf
+    fl += (P->sc.s1_nodes + right_leaves) * FLOP_ABC_S1 + P->sc.s2_nodes * FLOP_ABC_JOIN;
+  }
+  P->abc_flops = fl;
+  if (P->rewrite) {
+    if (e == cudaSuccess) e = upload(&P->d_sinstr, P->rsc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases, P->rsc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets, P->rsc.sets);
+  } else {
+    if (e == cudaSuccess) e = upload(&P->d_instr, P->sc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases, P->sc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets, P->sc.sets);
+  }
+  if (e != cudaSuccess) { free_plan(P); return cuda_status(e); }
+  const int ncur = P->rewrite ? P->rsc.stored_currents + P->rsc.local_currents
+                              : P->sc.stored_currents + P->sc.local_currents;
+  const AbcLayout L = abc_layout(k, mixed ? 4 : 8, ncur);
+  P->team_bytes = L.bytes;
+  P->block = std::max(128, P->kc.team);
+  P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  while (P->smem > (size_t)dev_smem && P->block > P->kc.team && P->block > 32) {
+    P->block /= 2;
+    P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  }
+  if (P->smem > (size_t)dev_smem) { free_plan(P); return QED_EUNSUPPORTED; }
+  e = cudaFuncSetAttribute((const void*)P->kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc.fn, P->block, P->smem);
+  if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
+  P->grid = per_sm * sms;
+  *out = P;
+  return QED_OK;
+}
+
 qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
   if (!P || !info) return QED_EINVAL;
   std::memset(info, 0, sizeof(*info));
@@ -358,6 +442,10 @@ qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
     info->s2_nodes = P->rsc.joins;
   }
   info->flops_literal_s2_per_point = sc.flops_literal_s2;
+  if (P->abc) {
+    info->flops_per_point = info->flops_executed_per_point = P->abc_flops;
+    info->flops_literal_s2_per_point = 0;
+  }
   info->team_threads = P->kc.team;
   info->smem_bytes_per_team = P->team_bytes;
   info->precision = (int)P->prec;

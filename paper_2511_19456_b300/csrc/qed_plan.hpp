@@ -15,6 +15,7 @@ struct KernelChoice {
 KernelChoice forward_kernel(int k, bool summed, bool mixed);
 KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
 KernelChoice rewrite_kernel(int k, bool summed, bool mixed);
+KernelChoice abc_kernel_for(int k, bool mixed, bool rewrite);
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
 }  // namespace qed
@@ -46,6 +47,10 @@ struct qed_plan_s {
   bool has_adj = false;
   // distributively rewritten DAG (qed_plan_create_rewrite)
   bool rewrite = false;
+  // ABC model (qed_abc_plan_create): scalar currents, A and C masses
+  bool abc = false;
+  double mass_c = 0.0;
+  long long abc_flops = 0;
   RwSchedule rsc;
   SumInstr* d_sinstr = nullptr;
   uint16_t* d_lane_tab = nullptr;   // spin-summed rewrite plans: leaf variants per (set, lane)

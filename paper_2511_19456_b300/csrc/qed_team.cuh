@@ -12,7 +12,8 @@ namespace qed {
 
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
-  if constexpr (TEAM <= 32) __syncwarp();
+  if constexpr (TEAM == 1) return;      // a thread sees its own shared-memory writes
+  else if constexpr (TEAM <= 32) __syncwarp();
   else __syncthreads();
 }
 
@@ -35,11 +36,7 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
   return v;
 }
 
-// Currents live in shared memory component-major: a node whose current has
-// nv spin variants occupies 4*nv complex slots starting at 4*base, component
-// c of variant v at slot 4*base + c*nv + v.  Threads that work on
-// neighbouring variants then touch neighbouring 8- (FP32) or 16-byte (FP64)
-// words, free of bank conflicts.
+// Complex pairs of the working precision (the adjoint's accumulators).
 template <typename Real> struct C2;
 template <> struct C2<float> { using T = float2; };
 template <> struct C2<double> { using T = double2; };

@@ -47,6 +47,24 @@ QED_HD TeamLayout team_layout(int k, int real_size, int ncur) {
   return L;
 }
 
+// Shared memory of one team of the ABC-model kernels: momenta (FP64), 1/D of
+// every subset, a reduction scratch and the (scalar) currents.
+struct AbcLayout {
+  int mom, inv, red, cur, bytes;
+};
+
+QED_HD AbcLayout abc_layout(int k, int real_size, int ncur) {
+  const int n = k + 1;
+  AbcLayout L;
+  int off = 0;
+  L.mom = off; off = align16(off + (k + 3) * 4 * 8);
+  L.inv = off; off = align16(off + (1 << n) * real_size);
+  L.red = off; off = align16(off + 16 * 8);
+  L.cur = off; off = align16(off + ncur * real_size);
+  L.bytes = off;
+  return L;
+}
+
 // Extra shared memory of the adjoint kernel after the forward team layout:
 // adjoints of every current, the amplitude seeds conj(M), and FP64
 // accumulators of the propagator (4 Dirac components + 1, complex) and
@@ -88,8 +106,9 @@ struct KParams {
   int ncur;          // stored + local currents
   int ncur_stored;   // currents kept for the whole point
   int team_bytes;
-  double mass;
-  double coupling;   // e^(2n)
+  double mass;       // electron mass; the A mass in the ABC model
+  double mass_c;     // ABC model: the C mass
+  double coupling;   // e^(2n); g^(2n) in the ABC model
   int fixed_sin, fixed_sout;       // helicity bit (0: +1, 1: -1)
   unsigned fixed_pol_bits;         // bit j: polarisation of photon j (0: pol 1, 1: pol 2)
 };

@@ -181,6 +181,44 @@ def points(k: int, n_points: int, omega: float, seed: int, mass: float = 1.0) ->
     return rambo(n_points, k, omega, seed, mass)
 
 
+def abc_points(k: int, n_points: int, rs: float, seed: int, mass_a: float = 1.0,
+               mass_b: float = 0.5) -> np.ndarray:
+    """A(p) + B(k_0) -> A(p') + k B points for the ABC model: the A at rest,
+    the B along +z with the energy that gives CM energy rs, and the final
+    state from flat massive (k+1)-body RAMBO phase space, boosted to the lab.
+    Slots as for QED: 0 = A in, 1 = B in, 2 = A out, 3.. = B out."""
+    s = rs * rs
+    e_b = (s - mass_a * mass_a - mass_b * mass_b) / (2.0 * mass_a)
+    kz = math.sqrt(max(0.0, e_b * e_b - mass_b * mass_b))
+    masses = np.full(k + 1, mass_b)
+    masses[0] = mass_a
+    final = rambo_cm(n_points, masses, rs, seed)
+    final = _lab_boost(final, kz / (mass_a + e_b))
+    final = onshell(final, masses)
+    p_in = np.zeros((n_points, 4))
+    p_in[:, 0] = mass_a
+    k_in = np.zeros((n_points, 4))
+    k_in[:, 0] = e_b
+    k_in[:, 3] = kz
+    return np.ascontiguousarray(np.concatenate([p_in[:, None], k_in[:, None], final], axis=1))
+
+
+# ABC-model workloads: A B -> A + k B, k odd; masses m_A = 1, m_B = 0.5,
+# m_C = 1.2 (no internal line can go on shell: m_A < m_C + m_B and
+# m_C < m_A + m_B), CM energy 2 above the final-state threshold m_A + k m_B.
+ABC_MASSES = dict(mass_a=1.0, mass_b=0.5, mass_c=1.2)
+ABC_WORKLOADS = {
+    f"abc_k{k}": dict(k=k, n_points=(1 << 20) if k < 7 else (1 << 17), rs=1.0 + 0.5 * k + 2.0, seed=10 + k)
+    for k in (1, 3, 5, 7)
+}
+
+
+def abc_workload_points(name: str, n_points: int | None = None) -> np.ndarray:
+    w = ABC_WORKLOADS[name]
+    return abc_points(w["k"], w["n_points"] if n_points is None else n_points, w["rs"], w["seed"],
+                      ABC_MASSES["mass_a"], ABC_MASSES["mass_b"])
+
+
 # --------------------------------------------------------------- workloads
 # Fixed helicity / polarisation of the k = 6 workload: e- in +, e- out +,
 # every photon in polarisation 1 (the linear "x-like" state).

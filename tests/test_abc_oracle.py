@@ -43,9 +43,10 @@ def boost(p, beta):
     return out
 
 
-def test_k1_is_the_s_plus_u_channel_closed_form():
-    mom = ps.points(1, 64, 1.0, seed=11)
-    for ma, mc, g in ((1.0, 1.0, 1.0), (1.0, 0.3, 0.7), (1.0, 0.55, 1.3)):
+@pytest.mark.parametrize("mass_b", [0.0, 0.5])
+def test_k1_is_the_s_plus_u_channel_closed_form(mass_b):
+    mom = ps.abc_points(1, 64, 3.0, seed=11, mass_a=1.0, mass_b=mass_b)
+    for ma, mc, g in ((1.0, 1.0, 1.0), (1.0, 0.3, 0.7), (1.0, 1.2, 1.3)):
         got = abc.m2(mom, mass_a=ma, mass_c=mc, coupling=g)
         s = np.array([mdot(p[0] + p[1], p[0] + p[1]) for p in mom])
         u = np.array([mdot(p[0] - p[3], p[0] - p[3]) for p in mom])
