@@ -362,6 +362,46 @@ def run_abc(args):
     print(json.dumps(res), flush=True)
 
 
+def run_sweep(args):
+    """Node-reduction sweep (paper Sec. III-E, Fig. f_optimization): the CDAG
+    of e- gamma -> e- + 4 gamma, one fixed spin state, FP64, executed node by
+    node after 0, 10, ..., all 140 single node reductions.  For each state:
+    nodes, FLOPs per point, points/s, the measured speed-up over the
+    unreduced state and the one predicted from the FLOPs; then the scheduled
+    kernel of the fully reduced DAG for comparison."""
+    import torch
+    from paper_2511_19456_b300 import Plan, TapePlan, reduction_steps
+    torch.cuda.set_device(0)
+    k = 4
+    hel = [1, 2, -1] + [1 + (j % 2) for j in range(k)]
+    n = args.n_points or 262144
+    mom = torch.from_numpy(ps.points(k, n, 4.0, 2)).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    S = reduction_steps(k)
+    states = []
+    for st in list(range(0, S, 10)) + [S]:
+        plan = TapePlan(k, hel, st)
+        inf = plan.info()
+        ms = time_calls(lambda: plan.eval(mom, out), args.steps, args.warmup)
+        states.append({"steps": st, "nodes": inf["nodes_reduced"], "compute_nodes": inf["compute_reduced"],
+                       "flops_per_point": inf["flops_per_point"], "smem_bytes_per_team": inf["smem_bytes_per_team"],
+                       "ms": ms, "points_per_s": n / (ms * 1e-3),
+                       "tflops": inf["flops_per_point"] * n / (ms * 1e-3) / 1e12})
+    for s_ in states:
+        s_["speedup_measured"] = states[0]["ms"] / s_["ms"]
+        s_["speedup_from_flops"] = states[0]["flops_per_point"] / s_["flops_per_point"]
+    plan = Plan(k, summed=False, hel=hel)
+    ms = time_calls(lambda: plan.eval(mom, out), args.steps, args.warmup)
+    res = {"workload": "reduction_sweep", "data": "synthetic", "metric": METRIC, "unit": "points/s",
+           "steps": args.steps, "warmup": args.warmup, "total_reductions": S, "states": states,
+           "scheduled_reduced_kernel": {"points_per_s": n / (ms * 1e-3), "ms": ms,
+                                        "speedup_over_unreduced_tape": states[0]["ms"] / ms},
+           "value": states[-1]["points_per_s"],
+           "config": {"workload": "reduction_sweep", "k": k, "n_points": n, "omega": 4.0, "hel": hel,
+                      "precision": "fp64"}}
+    print(json.dumps(res), flush=True)
+
+
 def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     import torch
     for _ in range(warmup):
@@ -386,7 +426,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched", "rewrite_vs_plain", "abc"],
+    ap.add_argument("--workload", default="compton_k4", choices=sorted(ps.WORKLOADS) + ["batched", "rewrite_vs_plain", "abc", "reduction_sweep"],
                     help="compton_k4 is the headline line; the others measure the other "
                          "configurations (adjoint at k = 6, k = 7, the batched stream)")
     ap.add_argument("--fp64-steps", type=int, default=None,
@@ -404,7 +444,7 @@ def main():
                          "rewrite: the distributively rewritten DAG (one current per photon subset)")
     args = ap.parse_args()
     if args.impl == "reference":
-        if args.workload in ("batched", "rewrite_vs_plain", "abc"):
+        if args.workload in ("batched", "rewrite_vs_plain", "abc", "reduction_sweep"):
             print(json.dumps({"impl": "reference", "unavailable":
                               "the batched stream is measured against the FP64 GPU path"}))
             return
@@ -415,6 +455,9 @@ def main():
         return
     if args.workload == "abc":
         run_abc(args)
+        return
+    if args.workload == "reduction_sweep":
+        run_sweep(args)
         return
     if args.workload != "compton_k4" and args.only is None and args.dag == "plain":
         run_other(args)

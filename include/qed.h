@@ -96,6 +96,7 @@ typedef struct {
   int team_threads;            /* threads cooperating on one point         */
   int smem_bytes_per_team;
   int precision;               /* qed_precision                            */
+  int reduction_steps;         /* tape plans: node reductions applied      */
 } qed_plan_info_t;
 
 /* Counts of the CDAG of one spin state, computed on the host without a GPU
@@ -166,6 +167,41 @@ typedef struct {
  * non-finite mass, a non-finite coupling. */
 qed_status qed_abc_plan_create(const qed_abc_process* process, qed_precision precision, int rewrite,
                                qed_plan_t* out);
+
+/* The node-reduction sweep (paper Sec. III-E, Fig. f_optimization).
+ *
+ * qed_reduction_steps: the number of single node reductions that take the
+ * per-diagram CDAG of e- gamma -> e- + k gamma (k in 1..6, one spin state)
+ * to its fixpoint. One step merges the first group, in topological order, of
+ * compute nodes with the same function and the same parents. The group's
+ * output data nodes merge with them (App. C).
+ *
+ * qed_tape_plan_create: a plan that executes, node by node, the CDAG after
+ * `reduction_steps` such steps (or after all of them, if the fixpoint comes
+ * first). Each compute node does its own work, its own propagator included,
+ * so the FLOPs per point are those of the DAG in that state.
+ *   - Arguments: k in 1..5, one fixed spin state (spin->summed == 0), FP64.
+ *   - Accepted: qed_eval, qed_eval_host, qed_plan_info. qed_plan_info's
+ *     nodes_reduced is the node count of that state, and reduction_steps
+ *     the steps applied.
+ *   - Every state gives the same |M|^2, bit for bit.
+ *   - Errors: QED_EINVAL for bad arguments; QED_EUNSUPPORTED when a team's
+ *     value slots exceed shared memory. */
+qed_status qed_reduction_steps(int k, int* steps);
+
+/* The tape of a reduction state, for inspection and CPU tests.
+ *   - Call it with instr == levels == NULL to get the sizes, then with
+ *     buffers of n_instr * 16 bytes (TapeInstr in csrc/dag.hpp) and
+ *     n_levels + 1 ints.
+ *   - Level l runs instructions levels[l] .. levels[l+1]-1.
+ *   - Errors: QED_EINVAL for k outside 1..5 or steps < 0. */
+typedef struct {
+  int k, n, steps, n_slots, n_diag, n_instr, n_levels;
+  long long nodes, compute_nodes, flops;
+} qed_tape_desc_t;
+qed_status qed_tape_export(int k, int steps, qed_tape_desc_t* desc, void* instr, int* levels);
+qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* spin, int reduction_steps,
+                                qed_plan_t* out);
 
 qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 

@@ -8,5 +8,5 @@ sm_103a CUDA kernels behind a C-ABI (include/qed.h).
     plan = Plan(k=4, summed=True, precision="fp64")
     m2 = plan.eval(momenta)          # momenta: cuda float64 [N, k+3, 4]
 """
-from .api import (AbcPlan, Batch, Plan, cross_section, dag_counts, generate, measure_fma_peak,  # noqa: F401
+from .api import (AbcPlan, Batch, Plan, TapePlan, reduction_steps, tape_export, cross_section, dag_counts, generate, measure_fma_peak,  # noqa: F401
                   schedule_export)

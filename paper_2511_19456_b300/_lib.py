@@ -31,6 +31,11 @@ class AbcProcess(ctypes.Structure):
                 ("mass_c", ctypes.c_double), ("coupling", ctypes.c_double)]
 
 
+class TapeDesc(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in ("k", "n", "steps", "n_slots", "n_diag", "n_instr", "n_levels")] + \
+               [(f, ctypes.c_longlong) for f in ("nodes", "compute_nodes", "flops")]
+
+
 class SpinCfg(ctypes.Structure):
     _fields_ = [("summed", ctypes.c_int), ("hel", ctypes.c_byte * 10)]
 
@@ -45,7 +50,7 @@ class PlanInfo(ctypes.Structure):
                 ("flops_executed_per_point", ctypes.c_longlong),
                 ("flops_literal_s2_per_point", ctypes.c_longlong),
                 ("team_threads", ctypes.c_int), ("smem_bytes_per_team", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("reduction_steps", ctypes.c_int)]
 
 
 class DagCounts(ctypes.Structure):
@@ -74,6 +79,11 @@ SIGNATURES = [
     ("qed_abc_plan_create", ctypes.c_int, [ctypes.POINTER(AbcProcess), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(_vp)]),
     ("qed_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    ("qed_reduction_steps", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("qed_tape_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(TapeDesc), _vp,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    ("qed_tape_plan_create", ctypes.c_int, [ctypes.POINTER(Process), ctypes.POINTER(SpinCfg), ctypes.c_int,
+                                            ctypes.POINTER(_vp)]),
     ("qed_eval", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),
     ("qed_eval_grad", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, _vp]),
     ("qed_eval_host", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),

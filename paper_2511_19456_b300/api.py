@@ -157,6 +157,56 @@ class AbcPlan(Plan):
         self.coupling = float(coupling)
 
 
+class TapePlan(Plan):
+    """Node-by-node execution of the CDAG of e- gamma -> e- + k gamma (one
+    fixed spin state, k <= 5, FP64) after `reduction_steps` single node
+    reductions: the node-reduction sweep of the paper's Sec. III-E."""
+
+    def __init__(self, k: int, hel, reduction_steps: int, mass: float = 1.0, charge: float = 1.0):
+        if hel is None or len(hel) != k + 3:
+            raise ValueError("a fixed state needs hel with k+3 entries")
+        proc = _lib.Process(int(k), float(mass), float(charge))
+        spin = _lib.SpinCfg()
+        spin.summed = 0
+        for i, v in enumerate(hel):
+            spin.hel[i] = int(v)
+        handle = ctypes.c_void_p()
+        check(_lib.lib().qed_tape_plan_create(ctypes.byref(proc), ctypes.byref(spin), int(reduction_steps),
+                                              ctypes.byref(handle)), "qed_tape_plan_create")
+        self._h = handle
+        self.rewrite = False
+        self.k = int(k)
+        self.summed = False
+        self.hel = list(hel)
+        self.precision = "fp64"
+        self.mass = float(mass)
+
+
+def reduction_steps(k: int) -> int:
+    """Single node reductions from the per-diagram CDAG to its fixpoint."""
+    out = ctypes.c_int()
+    check(_lib.lib().qed_reduction_steps(int(k), ctypes.byref(out)), "qed_reduction_steps")
+    return out.value
+
+
+TAPE_DTYPE = np.dtype([("op", "u1"), ("side", "u1"), ("arg", "u1"), ("pad", "u1"), ("mask", "<u2"),
+                       ("dst", "<u2"), ("src0", "<u2"), ("src1", "<u2"), ("pad2", "<u4")])
+
+
+def tape_export(k: int, steps: int) -> dict:
+    """The tape of the CDAG after `steps` node reductions (see TapePlan)."""
+    L = _lib.lib()
+    d = _lib.TapeDesc()
+    check(L.qed_tape_export(int(k), int(steps), ctypes.byref(d), None, None), "qed_tape_export")
+    instr = np.zeros(d.n_instr, dtype=TAPE_DTYPE)
+    levels = np.zeros(d.n_levels + 1, dtype=np.int32)
+    check(L.qed_tape_export(int(k), int(steps), ctypes.byref(d), instr.ctypes.data_as(ctypes.c_void_p),
+                            levels.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "qed_tape_export")
+    out = {f: getattr(d, f) for f, _ in _lib.TapeDesc._fields_}
+    out.update(instr=instr, levels=levels)
+    return out
+
+
 def dag_counts(k: int) -> dict:
     """Node counts of the per-diagram CDAG and of its node-reduced form."""
     c = _lib.DagCounts()

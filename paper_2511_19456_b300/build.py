@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqedm2.so")
-SOURCES = ["dag.cpp", "qed_api.cpp", "qed_fwd.cu", "qed_rw.cu", "abc_kernel.cu", "qed_adj.cu", "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu"]
+SOURCES = ["dag.cpp", "qed_api.cpp", "qed_fwd.cu", "qed_rw.cu", "abc_kernel.cu", "qed_tape.cu", "qed_adj.cu", "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu"]
 HEADERS = ["dag.hpp", "qed_types.h", "qed_device.cuh", "qed_team.cuh", "qed_eval.cuh", "qed_plan.hpp", "qed_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -159,6 +159,212 @@ Dag reduce(const Dag& in, std::vector<int32_t>* rep_out) {
 
 int nvar(bool summed, int level) { return summed ? (1 << (level + 1)) : 1; }
 
+bool reduce_step(Dag& g) {
+  const int N = g.size();
+  // the first group of equal compute nodes (function and parent set)
+  std::unordered_map<std::vector<int64_t>, int32_t, KeyHash> first;
+  std::vector<int32_t> leader(N, -1);
+  std::vector<int> group_size(N, 0);
+  std::vector<int64_t> key;
+  int chosen = -1;
+  for (int i = 0; i < N && chosen < 0; ++i) {
+    if (g.kind[i] == K_DATA) continue;
+    std::vector<int32_t> par(g.parents.begin() + g.pbeg[i], g.parents.begin() + g.pbeg[i + 1]);
+    std::sort(par.begin(), par.end());
+    key.assign({(int64_t)g.kind[i], (int64_t)g.fn[i]});
+    for (int32_t p : par) key.push_back(p);
+    auto it = first.find(key);
+    if (it == first.end()) {
+      first.emplace(key, i);
+    } else {
+      chosen = it->second;   // equal to an earlier node: this class is the first one complete
+    }
+  }
+  if (chosen < 0) return false;
+  // all members of the chosen class (they may lie after the one found)
+  std::vector<int32_t> cpar(g.parents.begin() + g.pbeg[chosen], g.parents.begin() + g.pbeg[chosen + 1]);
+  std::sort(cpar.begin(), cpar.end());
+  std::vector<char> merged(N, 0);
+  for (int i = chosen + 1; i < N; ++i) {
+    if (g.kind[i] != g.kind[chosen] || g.fn[i] != g.fn[chosen]) continue;
+    std::vector<int32_t> par(g.parents.begin() + g.pbeg[i], g.parents.begin() + g.pbeg[i + 1]);
+    std::sort(par.begin(), par.end());
+    if (par == cpar) merged[i] = 1;
+  }
+  // output data node of each compute node
+  std::vector<int32_t> out_data(N, -1);
+  for (int i = 0; i < N; ++i)
+    if (g.kind[i] == K_DATA && g.pbeg[i + 1] - g.pbeg[i] == 1) out_data[g.parents[g.pbeg[i]]] = i;
+  const int keep_data = out_data[chosen];
+  // rebuild: merged nodes and their data nodes map to the kept ones
+  Dag out;
+  std::vector<int32_t> rep(N, -1);
+  std::vector<int32_t> par;
+  for (int i = 0; i < N; ++i) {
+    if (merged[i]) { rep[i] = rep[chosen]; continue; }
+    if (g.kind[i] == K_DATA && g.pbeg[i + 1] - g.pbeg[i] == 1 && merged[g.parents[g.pbeg[i]]]) {
+      rep[i] = rep[keep_data];
+      continue;
+    }
+    par.clear();
+    for (int p = g.pbeg[i]; p < g.pbeg[i + 1]; ++p) par.push_back(rep[g.parents[p]]);
+    rep[i] = out.add((NodeKind)g.kind[i], g.fn[i], par.data(), (int)par.size());
+  }
+  g = std::move(out);
+  return true;
+}
+
+int reduction_steps(int k) {
+  Dag g = generate(k);
+  int s = 0;
+  while (reduce_step(g)) ++s;
+  return s;
+}
+
+Tape build_tape(int k, int steps) {
+  if (k < 1 || k > 6) throw std::runtime_error("k out of range");
+  Tape t;
+  t.k = k;
+  t.n = k + 1;
+  const int n = t.n;
+  const uint32_t all = (1u << n) - 1;
+  Dag g = generate(k);
+  while (t.steps < steps && reduce_step(g)) ++t.steps;
+  t.counts = g.counts();
+  const int N = g.size();
+  std::vector<int32_t> producer(N, -1);
+  for (int i = 0; i < N; ++i)
+    if (g.kind[i] == K_DATA && g.pbeg[i + 1] - g.pbeg[i] == 1) producer[i] = g.parents[g.pbeg[i]];
+  // per compute node: op, side, photon set, level
+  std::vector<int> op(N, 0), side(N, -1), level(N, -1), photon(N, -1);
+  std::vector<uint32_t> set(N, 0);
+  int sum_node = -1;
+  for (int i = 0; i < N; ++i) {
+    const int np = g.pbeg[i + 1] - g.pbeg[i];
+    const int32_t* pp = g.parents.data() + g.pbeg[i];
+    switch (g.kind[i]) {
+      case K_U: {
+        const int s = g.fn[i];
+        level[i] = 0;
+        if (s == 0 || s == 2) { op[i] = T_SPINOR; side[i] = s == 0 ? 0 : 1; }
+        else { op[i] = T_POL; photon[i] = s == 1 ? 0 : s - 2; }
+        break;
+      }
+      case K_V: {
+        int cur = -1, ph = -1;
+        for (int a = 0; a < np; ++a) {
+          const int c = producer[pp[a]];
+          if (op[c] == T_POL) ph = c; else cur = c;
+        }
+        if (cur < 0 || ph < 0 || np != 2) throw std::runtime_error("tape: malformed V");
+        op[i] = T_V;
+        side[i] = side[cur];
+        photon[i] = photon[ph];
+        set[i] = set[cur] | (1u << photon[ph]);
+        level[i] = std::max(level[cur], level[ph]) + 1;
+        break;
+      }
+      case K_S1: {
+        const int c = producer[pp[0]];
+        op[i] = T_S1;
+        side[i] = side[c];
+        set[i] = set[c];
+        level[i] = level[c] + 1;
+        break;
+      }
+      case K_S2: {
+        int a = producer[pp[0]], b = producer[pp[1]];
+        if (side[a] == 1) std::swap(a, b);
+        op[i] = T_S2;
+        set[i] = set[a];
+        level[i] = std::max(level[a], level[b]) + 1;
+        break;
+      }
+      case K_SUM:
+        sum_node = i;
+        break;
+      default:
+        break;
+    }
+  }
+  if (sum_node < 0) throw std::runtime_error("tape: no Sum node");
+  // diagram index of each S2: its position among the Sum's parents
+  std::vector<int> diag(N, -1);
+  for (int p = g.pbeg[sum_node]; p < g.pbeg[sum_node + 1]; ++p) diag[producer[g.parents[p]]] = t.n_diag++;
+  // last level at which each value is read
+  std::vector<int> last_use(N, -1);
+  int max_level = 0;
+  for (int i = 0; i < N; ++i) {
+    if (!op[i]) continue;
+    max_level = std::max(max_level, level[i]);
+    for (int p = g.pbeg[i]; p < g.pbeg[i + 1]; ++p) {
+      const int c = producer[g.parents[p]];
+      last_use[c] = std::max(last_use[c], level[i]);
+    }
+  }
+  // slots: before level L, free the values last read below L; values made
+  // at L get slots not read at L
+  std::vector<std::vector<int>> by_level(max_level + 1);
+  for (int i = 0; i < N; ++i)
+    if (op[i]) by_level[level[i]].push_back(i);
+  std::vector<int> slot(N, -1), free_slots;
+  std::vector<std::vector<int>> dies(max_level + 2);
+  for (int i = 0; i < N; ++i)
+    if (op[i] && op[i] != T_S2) dies[std::max(last_use[i], level[i]) + 1].push_back(i);
+  t.level_beg.push_back(0);
+  for (int L = 0; L <= max_level; ++L) {
+    for (int v : dies[L]) free_slots.push_back(slot[v]);
+    std::sort(free_slots.begin(), free_slots.end(), std::greater<int>());
+    for (int i : by_level[L]) {
+      TapeInstr in{};
+      in.op = (uint8_t)op[i];
+      in.side = (uint8_t)std::max(0, side[i]);
+      if (op[i] == T_S2) {
+        in.dst = (uint16_t)diag[i];
+      } else {
+        int sl;
+        if (!free_slots.empty()) { sl = free_slots.back(); free_slots.pop_back(); }
+        else sl = t.n_slots++;
+        slot[i] = sl;
+        in.dst = (uint16_t)sl;
+      }
+      const int32_t* pp = g.parents.data() + g.pbeg[i];
+      switch (op[i]) {
+        case T_SPINOR: in.arg = (uint8_t)(side[i] == 0 ? 0 : 2); t.flops += FLOP_SPINOR; break;
+        case T_POL: in.arg = (uint8_t)photon[i]; t.flops += FLOP_POL; break;
+        case T_V: {
+          int cur = producer[pp[0]], ph = producer[pp[1]];
+          if (op[cur] == T_POL) std::swap(cur, ph);
+          in.arg = (uint8_t)photon[i];
+          in.src0 = (uint16_t)slot[cur];
+          in.src1 = (uint16_t)slot[ph];
+          t.flops += FLOP_V;
+          break;
+        }
+        case T_S1:
+          in.src0 = (uint16_t)slot[producer[pp[0]]];
+          in.mask = (uint16_t)(side[i] == 0 ? set[i] : all & ~set[i]);
+          t.flops += FLOP_SUBSET + FLOP_S1;
+          break;
+        case T_S2: {
+          int a = producer[pp[0]], b = producer[pp[1]];
+          if (side[a] == 1) std::swap(a, b);
+          in.src0 = (uint16_t)slot[a];
+          in.src1 = (uint16_t)slot[b];
+          in.mask = (uint16_t)set[a];
+          t.flops += FLOP_SUBSET + FLOP_S1 + FLOP_JOIN;
+          break;
+        }
+      }
+      t.instr.push_back(in);
+    }
+    t.level_beg.push_back((int32_t)t.instr.size());
+  }
+  if (t.n_slots > 65535) throw std::runtime_error("tape: too many slots");
+  t.flops += (long long)t.n_diag * FLOP_SUM + 3;
+  return t;
+}
+
 namespace {
 
 struct VInfo {

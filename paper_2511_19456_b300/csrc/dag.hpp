@@ -148,6 +148,47 @@ RwSchedule build_rewrite_schedule(int k, bool summed, int group = 0);
 // of `team` threads.
 int rewrite_default_group(int k, bool summed, int team);
 
+// ------------------------------------------------ node-reduction sweep
+// One node reduction (App. C; Sec. III-E): the first group, in topological
+// order, of two or more compute nodes with the same function and the same
+// parents is merged into one node, together with their output data nodes,
+// and the children are rewired.  Returns false at the fixpoint.
+bool reduce_step(Dag& g);
+
+// Number of reduction steps from generate(k) to the fixpoint.
+int reduction_steps(int k);
+
+// A level-synchronous tape of a DAG (any reduction state) for one fixed spin
+// state, executed node by node: every compute node of the DAG does its own
+// work, including the propagator of its own momentum.
+enum TapeOp : uint8_t { T_SPINOR = 1, T_POL = 2, T_V = 3, T_S1 = 4, T_S2 = 5 };
+struct TapeInstr {
+  uint8_t op;
+  uint8_t side;     // 0: column current (from u), 1: row current (from ubar)
+  uint8_t arg;      // T_SPINOR: slot 0 or 2; T_POL, T_V: photon
+  uint8_t pad;
+  uint16_t mask;    // T_S1, T_S2: photon set of the propagator's momentum
+  uint16_t dst;     // value slot (T_S2: diagram index)
+  uint16_t src0;    // T_V, T_S1: current; T_S2: left current
+  uint16_t src1;    // T_V: polarisation; T_S2: right current
+  uint32_t pad2;
+};
+static_assert(sizeof(TapeInstr) == 16, "TapeInstr layout");
+
+struct Tape {
+  int k = 0, n = 0;
+  int steps = 0;                   // reductions applied
+  int n_slots = 0, n_diag = 0;     // value slots (8 reals each), diagrams
+  std::vector<TapeInstr> instr;    // by level
+  std::vector<int32_t> level_beg;  // instr range of each level (size levels + 1)
+  Counts counts;                   // of the DAG the tape executes
+  long long flops = 0;             // per point
+};
+
+// The tape of generate(k) after `steps` reduction steps (fewer if the
+// fixpoint comes first; Tape::steps says how many).
+Tape build_tape(int k, int steps);
+
 // Build the reduced DAG of process k and linearise it.  ls/rs: number of
 // left/right levels stored for the whole point (at most h-1 / r-1); deeper
 // levels are rebuilt for each photon set.  Throws std::runtime_error when the
@@ -162,6 +203,7 @@ constexpr int FLOP_SUBSET = 20; // Q_S, D_S = Q^2 - m^2, 1/D and scaled entries
 constexpr int FLOP_SQUARE = 4;  // |M|^2 of one state added to the spin sum
 constexpr int FLOP_SPINOR = 30;
 constexpr int FLOP_POL = 15;
+constexpr int FLOP_SUM = 2;     // one diagram added to M (complex)
 // ABC model (scalar currents; the vertex factor g is applied once as g^(2n))
 constexpr int FLOP_ABC_SUBSET = 9;  // Q_S^2 - m^2 (4 mul, 4 sub) and 1/D
 constexpr int FLOP_ABC_S1 = 1;      // current times 1/D

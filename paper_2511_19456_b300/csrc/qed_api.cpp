@@ -41,6 +41,8 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_phases_adj);
   cudaFree(p->d_sets_adj);
   cudaFree(p->d_sinstr);
+  cudaFree(p->d_tape);
+  cudaFree(p->d_levels);
   cudaFree(p->d_lane_tab);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
@@ -66,6 +68,7 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.mom = mom;
   kp.out = out;
   kp.n = n;
+  kp.k = P->k;
   kp.instr = P->d_instr;
   kp.sinstr = P->d_sinstr;
   kp.lane_tab = P->d_lane_tab;
@@ -94,6 +97,13 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.fixed_sout = P->fixed_sout;
   kp.fixed_pol_bits = 0;
   for (int j = 0; j < 8; ++j) kp.fixed_pol_bits |= (unsigned)(P->fixed_pol[j] & 1) << j;
+  if (P->is_tape) {
+    kp.tape = P->d_tape;
+    kp.tape_levels = P->d_levels;
+    kp.n_levels = (int)P->tp.level_beg.size() - 1;
+    kp.n_slots = P->tp.n_slots;
+    kp.n_diag = P->tp.n_diag;
+  }
   return kp;
 }
 
@@ -417,6 +427,103 @@ qed_status qed_abc_plan_create(const qed_abc_process* proc, qed_precision precis
   return QED_OK;
 }
 
+qed_status qed_reduction_steps(int k, int* steps) {
+  if (!steps || k < 1 || k > 6) return QED_EINVAL;
+  try {
+    *steps = reduction_steps(k);
+  } catch (const std::bad_alloc&) {
+    return QED_ENOMEM;
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  return QED_OK;
+}
+
+qed_status qed_tape_export(int k, int steps, qed_tape_desc_t* desc, void* instr, int* levels) {
+  if (!desc || k < 1 || k > 5 || steps < 0) return QED_EINVAL;
+  Tape t;
+  try {
+    t = build_tape(k, steps);
+  } catch (const std::bad_alloc&) {
+    return QED_ENOMEM;
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  desc->k = t.k; desc->n = t.n; desc->steps = t.steps; desc->n_slots = t.n_slots; desc->n_diag = t.n_diag;
+  desc->n_instr = (int)t.instr.size();
+  desc->n_levels = (int)t.level_beg.size() - 1;
+  desc->nodes = t.counts.total;
+  desc->compute_nodes = t.counts.total - t.counts.data;
+  desc->flops = t.flops;
+  if (instr) std::memcpy(instr, t.instr.data(), t.instr.size() * sizeof(TapeInstr));
+  if (levels) std::memcpy(levels, t.level_beg.data(), t.level_beg.size() * sizeof(int32_t));
+  return QED_OK;
+}
+
+qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* spin, int reduction_steps,
+                                qed_plan_t* out) {
+  if (!process || !spin || !out || reduction_steps < 0) return QED_EINVAL;
+  const int k = process->k;
+  if (k < 1 || k > 5 || spin->summed) return QED_EINVAL;
+  if (!(process->mass > 0.0) || !std::isfinite(process->mass) || !std::isfinite(process->charge))
+    return QED_EINVAL;
+  qed_plan_s* P = new (std::nothrow) qed_plan_s();
+  if (!P) return QED_ENOMEM;
+  P->k = k;
+  P->summed = false;
+  P->prec = QED_FP64;
+  P->mass = process->mass;
+  P->charge = process->charge;
+  P->is_tape = true;
+  for (int s = 0; s < k + 3; ++s) {
+    const int h = spin->hel[s];
+    const bool electron = s == 0 || s == 2;
+    if (electron ? (h != 1 && h != -1) : (h != 1 && h != 2)) { delete P; return QED_EINVAL; }
+  }
+  P->fixed_sin = spin->hel[0] == 1 ? 0 : 1;
+  P->fixed_sout = spin->hel[2] == 1 ? 0 : 1;
+  P->fixed_pol[0] = spin->hel[1] - 1;
+  for (int j = 1; j <= k; ++j) P->fixed_pol[j] = spin->hel[j + 2] - 1;
+  P->kc = tape_kernel();
+  int dev_smem = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e != cudaSuccess) { delete P; return cuda_status(e); }
+  try {
+    int ls, rs;
+    default_levels(k, false, &ls, &rs);
+    P->sc = build_schedule(k, false, ls, rs);
+    P->tp = build_tape(k, reduction_steps);
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return QED_ENOMEM;
+  } catch (...) {
+    delete P;
+    return QED_EUNSUPPORTED;
+  }
+  const TapeLayout L = tape_layout(k, P->tp.n_slots, P->tp.n_diag);
+  P->team_bytes = L.bytes;
+  P->block = P->kc.team;   // one team per block: the occupancy follows the team's slots
+  P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  while (P->smem > (size_t)dev_smem && P->block > P->kc.team) {
+    P->block /= 2;
+    P->smem = (size_t)(P->block / P->kc.team) * L.bytes;
+  }
+  if (P->smem > (size_t)dev_smem) { delete P; return QED_EUNSUPPORTED; }
+  e = upload(&P->d_tape, P->tp.instr);
+  if (e == cudaSuccess) e = upload(&P->d_levels, P->tp.level_beg);
+  if (e != cudaSuccess) { free_plan(P); return cuda_status(e); }
+  e = cudaFuncSetAttribute((const void*)P->kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc.fn, P->block, P->smem);
+  if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
+  P->grid = per_sm * sms;
+  *out = P;
+  return QED_OK;
+}
+
 qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
   if (!P || !info) return QED_EINVAL;
   std::memset(info, 0, sizeof(*info));
@@ -445,6 +552,17 @@ qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
   if (P->abc) {
     info->flops_per_point = info->flops_executed_per_point = P->abc_flops;
     info->flops_literal_s2_per_point = 0;
+  }
+  if (P->is_tape) {
+    const Counts& c = P->tp.counts;
+    info->nodes_reduced = c.total;
+    info->compute_reduced = c.total - c.data;
+    info->v_nodes = c.v;
+    info->s1_nodes = c.s1;
+    info->s2_nodes = c.s2;
+    info->flops_per_point = info->flops_executed_per_point = P->tp.flops;
+    info->flops_literal_s2_per_point = P->tp.flops;
+    info->reduction_steps = P->tp.steps;
   }
   info->team_threads = P->kc.team;
   info->smem_bytes_per_team = P->team_bytes;

@@ -16,6 +16,7 @@ KernelChoice forward_kernel(int k, bool summed, bool mixed);
 KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
 KernelChoice rewrite_kernel(int k, bool summed, bool mixed);
 KernelChoice abc_kernel_for(int k, bool mixed, bool rewrite);
+KernelChoice tape_kernel();
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
 }  // namespace qed
@@ -51,6 +52,11 @@ struct qed_plan_s {
   bool abc = false;
   double mass_c = 0.0;
   long long abc_flops = 0;
+  // node-by-node tape of a DAG in a given reduction state (qed_tape_plan_create)
+  bool is_tape = false;
+  Tape tp;
+  TapeInstr* d_tape = nullptr;
+  int* d_levels = nullptr;
   RwSchedule rsc;
   SumInstr* d_sinstr = nullptr;
   uint16_t* d_lane_tab = nullptr;   // spin-summed rewrite plans: leaf variants per (set, lane)

@@ -65,6 +65,22 @@ QED_HD AbcLayout abc_layout(int k, int real_size, int ncur) {
   return L;
 }
 
+// Shared memory of one team of the tape kernel: momenta, the value slots
+// (8 FP64 reals each) and the diagram amplitudes (complex FP64).
+struct TapeLayout {
+  int mom, val, diag, bytes;
+};
+
+QED_HD TapeLayout tape_layout(int k, int n_slots, int n_diag) {
+  TapeLayout L;
+  int off = 0;
+  L.mom = off;  off = align16(off + (k + 3) * 4 * 8);
+  L.val = off;  off = align16(off + n_slots * 8 * 8);
+  L.diag = off; off = align16(off + n_diag * 2 * 8);
+  L.bytes = off;
+  return L;
+}
+
 // Extra shared memory of the adjoint kernel after the forward team layout:
 // adjoints of every current, the amplitude seeds conj(M), and FP64
 // accumulators of the propagator (4 Dirac components + 1, complex) and
@@ -93,6 +109,7 @@ struct KParams {
   double* out;
   double* grad;      // adjoint kernel: d|M|^2/dk_j [N][k][3] (may be null otherwise)
   long long n;
+  int k;             // photons out
   const Instr* instr;
   const SumInstr* sinstr;   // rewritten-DAG instructions (rewrite plans)
   const Phase* phases;
@@ -111,6 +128,10 @@ struct KParams {
   double coupling;   // e^(2n); g^(2n) in the ABC model
   int fixed_sin, fixed_sout;       // helicity bit (0: +1, 1: -1)
   unsigned fixed_pol_bits;         // bit j: polarisation of photon j (0: pol 1, 1: pol 2)
+  // tape plans (node-reduction sweep)
+  const TapeInstr* tape;
+  const int* tape_levels;          // instruction range of each level
+  int n_levels, n_slots, n_diag;
 };
 
 }  // namespace qed

@@ -180,3 +180,50 @@ def evaluate_rewrite(sched, orc, point, fixed_hel=None, mass=1.0):
                 vl = vr = 0
             M[lam] += cur[se["leaf_r"] + vr] @ cur[se["leaf_l"] + vl]
     return float(np.sum(np.abs(M) ** 2))
+
+
+def evaluate_tape(tape, orc, point, fixed_hel, mass=1.0):
+    """Interpreter of a node-reduction-sweep tape (qed_tape_export): every
+    node computed as its task, one fixed spin state, diagrams summed in
+    order."""
+    k = tape["k"]
+    n = k + 1
+    g = [orc.gamma(mu) for mu in range(4)]
+    slot_of = [1] + [j + 2 for j in range(1, n)]
+
+    def prop(mask):
+        Q = point[0].copy()
+        for j in range(n):
+            if mask >> j & 1:
+                Q = Q + point[slot_of[j]] if j == 0 else Q - point[slot_of[j]]
+        D = Q[0] ** 2 - Q[1] ** 2 - Q[2] ** 2 - Q[3] ** 2 - mass * mass
+        return (_slash(g, Q) + mass * np.eye(4)) / D
+
+    sin = fixed_hel[0]
+    sout = fixed_hel[2]
+    pols = [fixed_hel[1]] + [fixed_hel[j + 2] for j in range(1, n)]
+    vals = {}
+    diag = np.zeros(tape["n_diag"], dtype=complex)
+    ins = tape["instr"]
+    lv = tape["levels"]
+    for L in range(tape["n_levels"]):
+        for i in range(lv[L], lv[L + 1]):
+            x = ins[i]
+            op, side = int(x["op"]), int(x["side"])
+            if op == 1:      # external spinor
+                vals[x["dst"]] = (orc.spinor(point[0], sin, mass) if side == 0
+                                  else orc.spinor(point[2], sout, mass, bar=True))
+            elif op == 2:    # polarisation
+                j = int(x["arg"])
+                vals[x["dst"]] = _slash(g, orc.polarisation(point[slot_of[j]], pols[j]))
+            elif op == 3:    # vertex
+                E = vals[x["src1"]]
+                c = vals[x["src0"]]
+                vals[x["dst"]] = E @ c if side == 0 else c @ E
+            elif op == 4:    # propagator
+                P = prop(int(x["mask"]))
+                c = vals[x["src0"]]
+                vals[x["dst"]] = P @ c if side == 0 else c @ P
+            elif op == 5:    # one diagram
+                diag[x["dst"]] = vals[x["src1"]] @ (prop(int(x["mask"])) @ vals[x["src0"]])
+    return float(abs(diag.sum()) ** 2)

@@ -143,3 +143,43 @@ def test_rewrite_schedule_structure(k):
     for t in range(4):
         used = ins["nterms"] > t
         assert np.all(ins["src"][used, t] < ncur)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_reduction_sweep_reaches_the_fixpoint(k):
+    """Single node reductions, applied one at a time, end in the same DAG as
+    the one-pass fixpoint (same node counts), every step removing nodes; the
+    unreduced state has the Table I count."""
+    from paper_2511_19456_b300 import reduction_steps, tape_export
+    S = reduction_steps(k)
+    c = dag_counts(k)
+    first = tape_export(k, 0)
+    assert first["nodes"] == c["unreduced_total"] == table1()[k]
+    last = tape_export(k, S)
+    assert last["steps"] == S and last["nodes"] == c["reduced_total"]
+    assert tape_export(k, S + 3)["steps"] == S
+    prev = first["nodes"]
+    for st in range(1, S + 1, max(1, S // 12)):
+        t = tape_export(k, st)
+        assert t["nodes"] < prev
+        prev = t["nodes"]
+    assert first["flops"] > last["flops"] or S == 0
+
+
+def test_reduction_step_count_k4():
+    """k = 4: one step per class of equal nodes: left levels 1..3 (5, 20 and
+    60 classes of V, 5 and 20 of S1) and right levels 1..2 (5 and 20 of V,
+    5 of S1): 140."""
+    from paper_2511_19456_b300 import reduction_steps
+    assert reduction_steps(4) == 140
+
+
+@pytest.mark.parametrize("k,steps", [(2, 0), (2, 4), (2, 9), (3, 0), (3, 17), (3, 40)])
+def test_tape_interpreter_matches_oracle(orc, k, steps):
+    from paper_2511_19456_b300 import tape_export
+    tape = tape_export(k, steps)
+    hel = [1, 2, -1] + [1 + (j % 2) for j in range(k)]
+    mom = ps.points(k, 3, 1.0 + k, seed=320 + k)
+    ref = orc.m2(mom, sum_mask=0, hel=hel)
+    got = np.array([schedule_interp.evaluate_tape(tape, orc, mom[i], hel) for i in range(len(mom))])
+    assert np.allclose(got, ref, rtol=1e-11, atol=0)
