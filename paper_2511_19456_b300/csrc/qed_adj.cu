@@ -286,7 +286,7 @@ qed_adj_kernel(const KParams p) {
                                       s_cur);
         team_sync<TEAM>();
       }
-      join_set<K, SUMMED, Real, TEAM, 1>(se, lane, s_cur, acc);
+      join_set<K, SUMMED, Real, TEAM, 1>(se, SUMMED ? p.lane_tab + ((size_t)s << N) : nullptr, lane, s_cur, acc);
       team_sync<TEAM>();
     }
 

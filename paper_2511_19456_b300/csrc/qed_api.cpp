@@ -278,25 +278,27 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
     delete P;
     return QED_EUNSUPPORTED;
   }
-  if (rewrite) {
-    if (P->summed) {
-      const int n = k + 1;
-      std::vector<uint16_t> tab(P->rsc.sets.size() << n);
-      for (size_t s = 0; s < P->rsc.sets.size(); ++s) {
-        const unsigned S = P->rsc.sets[s].mask, C = ((1u << n) - 1) & ~S;
-        for (unsigned c = 0; c < (1u << n); ++c) {
-          unsigned l = 0, r = 0;
-          int ol = 0, orr = 0;
-          for (int j = 0; j < n; ++j) {
-            const unsigned b = (c >> j) & 1u;
-            if (S & (1u << j)) l |= b << ol++;
-            if (C & (1u << j)) r |= b << orr++;
-          }
-          tab[(s << n) + c] = (uint16_t)(l | (r << 8));
+  if (P->summed) {
+    // lane table: leaf variants of every (photon set, polarisation pattern)
+    const int n = k + 1;
+    const auto& sets = rewrite ? P->rsc.sets : P->sc.sets;
+    std::vector<uint16_t> tab(sets.size() << n);
+    for (size_t s = 0; s < sets.size(); ++s) {
+      const unsigned S = sets[s].mask, C = ((1u << n) - 1) & ~S;
+      for (unsigned c = 0; c < (1u << n); ++c) {
+        unsigned l = 0, r = 0;
+        int ol = 0, orr = 0;
+        for (int j = 0; j < n; ++j) {
+          const unsigned b = (c >> j) & 1u;
+          if (S & (1u << j)) l |= b << ol++;
+          if (C & (1u << j)) r |= b << orr++;
         }
+        tab[(s << n) + c] = (uint16_t)(l | (r << 8));
       }
-      if (e == cudaSuccess) e = upload(&P->d_lane_tab, tab);
     }
+    if (e == cudaSuccess) e = upload(&P->d_lane_tab, tab);
+  }
+  if (rewrite) {
     if (e == cudaSuccess) e = upload(&P->d_sinstr, P->rsc.instr);
     if (e == cudaSuccess) e = upload(&P->d_phases, P->rsc.phases);
     if (e == cudaSuccess) e = upload(&P->d_sets, P->rsc.sets);

@@ -42,7 +42,7 @@ __device__ __forceinline__ void eval_point(const KParams& p, long long pt, bool 
       run_phase<TEAM, SUMMED, Real>(P, lane, p, s_q, s_eps, s_spin, s_cur);
       team_sync<TEAM>();
     }
-    join_set<K, SUMMED, Real, TEAM, ES>(se, lane, s_cur, acc);
+    join_set<K, SUMMED, Real, TEAM, ES>(se, SUMMED ? p.lane_tab + ((size_t)s << N) : nullptr, lane, s_cur, acc);
     team_sync<TEAM>();
   }
 

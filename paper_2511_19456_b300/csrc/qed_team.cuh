@@ -329,8 +329,10 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
 
 // The S2 joins of every diagram whose left photon set is se.mask (a6), summed
 // per spin state into acc (a7).
+// tab: the set's row of the plan's lane table (spin-summed: entry c holds
+// pext(c, S) | pext(c, not S) << 8).
 template <int K, bool SUMMED, typename Real, int TEAM, int ES>
-__device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Real* s_cur,
+__device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab, int lane, const Real* s_cur,
                                        Acc<Real>* acc) {
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;
@@ -344,11 +346,20 @@ __device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Rea
   constexpr int GA = NL % 3 == 0 ? 3 : (NL % 2 == 0 ? 2 : 1); // left leaves per compensated step
   constexpr int NSI = ES >= 2 ? 1 : 2;
   constexpr int NSO = ES >= 4 ? 1 : 2;
+  // mixed form: one compensated step for the whole set where it has at most
+  // 12 diagrams, else one per GA x BC block
+  constexpr bool ONE_STEP = NL * NR <= 12;
     if constexpr (SUMMED) {
       const unsigned c = (unsigned)lane & ALL;
       const int ep = lane >> N;
-      const int vl = ((int)pext_bits(c, se.mask, N) << 1) + (ES >= 2 ? (ep & 1) : 0);
-      const int vr = ((int)pext_bits(c, ALL & ~se.mask, N) << 1) + (ES >= 4 ? (ep >> 1) : 0);
+      const unsigned tv = __ldg(tab + c);
+      const int vl = ((int)(tv & 0xffu) << 1) + (ES >= 2 ? (ep & 1) : 0);
+      const int vr = ((int)(tv >> 8) << 1) + (ES >= 4 ? (ep >> 1) : 0);
+      float ys[NSI * NSO][2];
+      if constexpr (sizeof(Real) == 4 && ONE_STEP) {
+#pragma unroll
+        for (int i = 0; i < NSI * NSO; ++i) acc[i].start(ys[i][0], ys[i][1]);
+      }
 
       for (int b0 = 0; b0 < NR; b0 += BC) {
         Real rw[BC][NSO][8];
@@ -374,6 +385,12 @@ __device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Rea
 #pragma unroll
                   for (int bb = 0; bb < BC; ++bb)
                     dot_acc(rw[bb][so], lc[ga][si], acc[si * NSO + so].re, acc[si * NSO + so].im);
+              } else if constexpr (ONE_STEP) {
+#pragma unroll
+                for (int ga = 0; ga < GA; ++ga)
+#pragma unroll
+                  for (int bb = 0; bb < BC; ++bb)
+                    dot_acc(rw[bb][so], lc[ga][si], ys[si * NSO + so][0], ys[si * NSO + so][1]);
               } else {
                 // the GA x BC diagrams of this state in one compensated step
                 float yr, yi;
@@ -386,6 +403,10 @@ __device__ __forceinline__ void join_set(const SetEntry& se, int lane, const Rea
               }
             }
         }
+      }
+      if constexpr (sizeof(Real) == 4 && ONE_STEP) {
+#pragma unroll
+        for (int i = 0; i < NSI * NSO; ++i) acc[i].commit(ys[i][0], ys[i][1]);
       }
     } else {
       for (int q = lane; q < NL * NR; q += TEAM) {
