@@ -12,7 +12,8 @@
 //   2. seeds Mbar_l = conj(M_l) in shared memory;
 //   3. for every photon set S: rebuild the set's currents (sub-currents are
 //      recomputed, not stored), transposed joins give the leaf adjoints
-//        Lbar_a = sum_b sum_l Mbar_l R'_b,   R'bar_b = sum_a sum_l Mbar_l L_a,
+//        Lbar_a = sum_b sum_l Mbar_l R'_b,   R'bar_b = sum_a sum_l Mbar_l L_a
+//      (the same for every a, resp. b: the leaf sums are formed first),
 //      then the set's instructions in reverse order pass adjoints to their
 //      inputs and accumulate the parameter terms;
 //   4. the kept inner levels in reverse order;
@@ -87,13 +88,22 @@ __device__ __forceinline__ void atomic_add_cur(Real* p, int nv, const Real x[8])
   (void)nv;
 }
 
-// One instruction output variant v (polarisation pol): given its adjoint ybar
-// and its input x, accumulate the parameter terms and return the input's
-// adjoint contribution in xbar (added).
+// Parameter terms of one instruction output: the propagator bilinears
+// (s_mu, mu = 0..3, and u) of its post set and the polarisation terms e_i
+// (i = 1..3) of its photon, in the working precision.
 template <typename Real>
-__device__ __forceinline__ void backprop_one(const Instr& in, int pol, const Real x[8], const Real yb[8],
-                                             const Real* s_q, const Real* s_eps, double* s_acc_s,
-                                             double* s_acc_e, Real xbar[8]) {
+struct ParTerms {
+  Real s[10];   // s_0..s_3, u (complex)
+  Real e[6];    // e_1..e_3 (complex), already with the sign of eps/ = -gamma.eps
+};
+
+// One instruction output variant (polarisation pol): given its adjoint ybar
+// and its input x, add the parameter terms to T and the input's adjoint
+// contribution to xbar.
+template <typename Real>
+__device__ __forceinline__ void backprop_terms(const Instr& in, int pol, const Real x[8], const Real yb[8],
+                                               const Real* s_q, const Real* s_eps, ParTerms<Real>& T,
+                                               Real xbar[8]) {
   const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
   const Real ev[3] = {e3[0], e3[1], e3[2]};
   Real w[8], wb[8], t[8];
@@ -108,10 +118,10 @@ __device__ __forceinline__ void backprop_one(const Instr& in, int pol, const Rea
       bilinears(yb, w, s, u);                   // s_mu = ybar g^mu w
       Cf<Real> u2, sd[4];
       bilinears(yb, y, sd, u2);                 // u = ybar . y
-      double* A = s_acc_s + in.post * 10;
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) atomic_add_c(A + 2 * mu, (double)s[mu].re, (double)s[mu].im);
-      atomic_add_c(A + 8, (double)u2.re, (double)u2.im);
+      for (int mu = 0; mu < 4; ++mu) { T.s[2 * mu] += s[mu].re; T.s[2 * mu + 1] += s[mu].im; }
+      T.s[8] += u2.re;
+      T.s[9] += u2.im;
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
@@ -128,10 +138,10 @@ __device__ __forceinline__ void backprop_one(const Instr& in, int pol, const Rea
       bilinears(w, yb, s, u);                   // s_mu = w g^mu ybar
       Cf<Real> u2, sd[4];
       bilinears(y, yb, sd, u2);                 // u = y . ybar
-      double* A = s_acc_s + in.post * 10;
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) atomic_add_c(A + 2 * mu, (double)s[mu].re, (double)s[mu].im);
-      atomic_add_c(A + 8, (double)u2.re, (double)u2.im);
+      for (int mu = 0; mu < 4; ++mu) { T.s[2 * mu] += s[mu].re; T.s[2 * mu + 1] += s[mu].im; }
+      T.s[8] += u2.re;
+      T.s[9] += u2.im;
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
@@ -141,14 +151,18 @@ __device__ __forceinline__ void backprop_one(const Instr& in, int pol, const Rea
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) xbar[i] += t[i];
-  double* E = s_acc_e + (in.photon * 2 + pol) * 6;
 #pragma unroll
-  for (int i = 1; i < 4; ++i) atomic_add_c(E + 2 * (i - 1), -(double)s[i].re, -(double)s[i].im);
+  for (int i = 1; i < 4; ++i) { T.e[2 * (i - 1)] -= s[i].re; T.e[2 * (i - 1) + 1] -= s[i].im; }
 }
 
 // Reverse of one phase: every instruction passes its outputs' adjoints to its
-// input (atomic adds: siblings share inputs).  Summed spin: item vp = one
-// input variant and both photon polarisations.
+// input (atomic adds: siblings share inputs) and its parameter terms to the
+// FP64 accumulators.  Summed spin: item vp = one input variant and both
+// photon polarisations.  The G = min(2^level, TEAM, 32) consecutive lanes
+// that work on one instruction share its post set and photon: their
+// parameter terms are summed by shuffles first, and one lane of the group
+// adds them to the accumulators, so lanes do not contend for the same
+// shared-memory words.
 template <int TEAM, bool SUMMED, typename Real>
 __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const KParams& p,
                                                const Real* s_q, const Real* s_eps,
@@ -158,46 +172,96 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
   for (int slot = 0; slot < 2; ++slot) {
     const int cnt = ph.cnt[slot];
     if (cnt == 0) continue;
-    const int lg = SUMMED ? ph.level[slot] : 0;
-    const int total = cnt << lg;
-    for (int it = lane; it < total; it += TEAM) {
-      const int i = it >> lg;
-      const int vp = it & ((1 << lg) - 1);
-      const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
-      Real x[8], xb[8], yb[8];
+    if constexpr (SUMMED) {
+      constexpr int WMAX = TEAM < 32 ? TEAM : 32;
+      const int lg = ph.level[slot];
+      const int total = cnt << lg;
+      const int G = (1 << lg) < WMAX ? (1 << lg) : WMAX;
+      for (int base = 0; base < total; base += TEAM) {
+        // every lane of the warp runs the same rounds (the shuffles below)
+        const int it = base + lane;
+        const bool valid = it < total;
+        const int i = valid ? it >> lg : 0;
+        const int vp = it & ((1 << lg) - 1);
+        const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
+        ParTerms<Real> T[2];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
-      if constexpr (SUMMED) {
-        const int nv = 2 << in.level;
-        if (in.src < 0) load8(s_spin + (in.side * 2 + vp) * 8, x);
-        else load_cur(s_cur, in.src, nv >> 1, vp, x);
-        const int b = 1 + in.rank;
-        const int lo = vp & ((1 << b) - 1);
-        const int hi = (vp >> b) << (b + 1);
+        for (int q = 0; q < 2; ++q) {
 #pragma unroll
-        for (int pol = 0; pol < 2; ++pol) {
-          load_cur(s_adj, in.dst, nv, hi | (pol << b) | lo, yb);
-          backprop_one(in, pol, x, yb, s_q, s_eps, s_acc_s, s_acc_e, xb);
+          for (int c = 0; c < 10; ++c) T[q].s[c] = (Real)0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) T[q].e[c] = (Real)0;
         }
-      } else {
+        if (valid) {
+          Real x[8], xb[8], yb[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
+          const int nv = 2 << in.level;
+          if (in.src < 0) load8(s_spin + (in.side * 2 + vp) * 8, x);
+          else load_cur(s_cur, in.src, nv >> 1, vp, x);
+          const int b = 1 + in.rank;
+          const int lo = vp & ((1 << b) - 1);
+          const int hi = (vp >> b) << (b + 1);
+#pragma unroll
+          for (int pol = 0; pol < 2; ++pol) {
+            load_cur(s_adj, in.dst, nv, hi | (pol << b) | lo, yb);
+            backprop_terms(in, pol, x, yb, s_q, s_eps, T[pol], xb);
+          }
+          if (in.src >= 0) atomic_add_cur(s_adj + (size_t)(in.src + vp) * 8, 0, xb);
+        }
+        // the propagator terms do not depend on the polarisation
+#pragma unroll
+        for (int c = 0; c < 10; ++c) T[0].s[c] += T[1].s[c];
+        for (int off = 1; off < G; off <<= 1) {
+#pragma unroll
+          for (int c = 0; c < 10; ++c) T[0].s[c] += __shfl_xor_sync(0xffffffffu, T[0].s[c], off);
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) T[q].e[c] += __shfl_xor_sync(0xffffffffu, T[q].e[c], off);
+        }
+        if (valid && (vp & (G - 1)) == 0) {
+          if (in.post) {
+            double* A = s_acc_s + in.post * 10;
+#pragma unroll
+            for (int c = 0; c < 10; c += 2) atomic_add_c(A + c, (double)T[0].s[c], (double)T[0].s[c + 1]);
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            double* E = s_acc_e + (in.photon * 2 + q) * 6;
+#pragma unroll
+            for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T[q].e[c], (double)T[q].e[c + 1]);
+          }
+        }
+      }
+    } else {
+      for (int it = lane; it < cnt; it += TEAM) {
+        const Instr in = ld_instr(p.instr + ph.beg[slot] + it);
         const int pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
+        Real x[8], xb[8], yb[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
         if (in.src < 0) load8(s_spin + (in.side * 2 + (in.side == 0 ? p.fixed_sin : p.fixed_sout)) * 8, x);
         else load_cur(s_cur, in.src, 1, 0, x);
         load_cur(s_adj, in.dst, 1, 0, yb);
-        backprop_one(in, pol, x, yb, s_q, s_eps, s_acc_s, s_acc_e, xb);
+        ParTerms<Real> T;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) T.s[c] = (Real)0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) T.e[c] = (Real)0;
+        backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
+        if (in.post) {
+          double* A = s_acc_s + in.post * 10;
+#pragma unroll
+          for (int c = 0; c < 10; c += 2) atomic_add_c(A + c, (double)T.s[c], (double)T.s[c + 1]);
+        }
+        double* E = s_acc_e + (in.photon * 2 + pol) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T.e[c], (double)T.e[c + 1]);
+        if (in.src >= 0) atomic_add_cur(s_adj + (size_t)in.src * 8, 0, xb);
       }
-      if (in.src >= 0) atomic_add_cur(s_adj + (size_t)(in.src + vp) * 8, 0, xb);
     }
   }
-}
-
-// pdep: scatter the low bits of v into the set bits of mask.
-__device__ __forceinline__ unsigned pdep_bits(unsigned v, unsigned mask, int n) {
-  unsigned r = 0;
-  int o = 0;
-  for (int j = 0; j < n; ++j)
-    if (mask & (1u << j)) { r |= ((v >> o) & 1u) << j; ++o; }
-  return r;
 }
 
 // d eps_pol / d k_a (a = x, y, z) for the real linear polarisations; zero on
@@ -330,72 +394,74 @@ qed_adj_kernel(const KParams p) {
                                       s_cur);
         team_sync<TEAM>();
       }
-      const unsigned S = se.mask, SC = ALL & ~S;
-      if constexpr (SUMMED) {
-        // left leaves: item (a, vL), vL = si + 2 pS
-        for (int it = lane; it < NL * NVL + NR * NVR; it += TEAM) {
-          Real acc8[8];
+      // transposed joins.  M_l = sum_{a,b} R'_b[vR] . L_a[vL], so the adjoint
+      // of every left leaf a is the same, Lbar[vL] = sum_vR Mbar_l Rsum[vR]
+      // with Rsum = sum_b R'_b, and likewise Rbar[vR] = sum_vL Mbar_l Lsum[vL]:
+      // the leaf sums first (into the adjoint slots of leaf 1 of each side,
+      // or leaf 0 when a side has one leaf: free until the copies below),
+      // then one product per leaf variant into the adjoint slots of leaf 0,
+      // then a copy to every other leaf.
+      {
+        const int sum_l = NL > 1 ? se.leaf_l + NVL : se.leaf_l;
+        const int sum_r = NR > 1 ? se.leaf_r + NVR : se.leaf_r;
+        for (int it = lane; it < (NVL + NVR) * 8; it += TEAM) {
+          const bool left = it < NVL * 8;
+          const int q = left ? it : it - NVL * 8;
+          const int cnt = left ? NL : NR, nv = left ? NVL : NVR;
+          const Real* src = s_cur + (size_t)(left ? se.leaf_l : se.leaf_r) * 8;
+          Real sum = (Real)0;
+          for (int a = 0; a < cnt; ++a) sum += src[(size_t)a * nv * 8 + q];
+          s_adj[(size_t)(left ? sum_l : sum_r) * 8 + q] = sum;
+        }
+        team_sync<TEAM>();
+        constexpr int NITEM = (NVL + NVR) * 4;
+        constexpr int PER = (NITEM + TEAM - 1) / TEAM;
+        Real br[PER], bi[PER];
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc8[c] = (Real)0;
-          if (it < NL * NVL) {
-            const int a = it / NVL, vL = it - a * NVL;
-            const int si = vL & 1;
-            const unsigned cs = pdep_bits((unsigned)(vL >> 1), S, N);
-            for (int b = 0; b < NR; ++b)
-              for (int vR = 0; vR < NVR; ++vR) {
-                const int so = vR & 1;
-                const unsigned c = cs | pdep_bits((unsigned)(vR >> 1), SC, N);
-                const int lam = si | (so << 1) | (int)(c << 2);
-                const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
-                Real rw[8];
-                load_cur(s_cur, se.leaf_r + b * NVR, NVR, vR, rw);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  acc8[2 * q] += mr * rw[2 * q] - mi * rw[2 * q + 1];
-                  acc8[2 * q + 1] += mr * rw[2 * q + 1] + mi * rw[2 * q];
-                }
-              }
-            store_cur(s_adj, se.leaf_l + a * NVL, NVL, vL, acc8);
+        for (int k2 = 0; k2 < PER; ++k2) {
+          const int it = lane + k2 * TEAM;
+          br[k2] = bi[k2] = (Real)0;
+          if (it >= NITEM) continue;
+          // item (side, variant v, Dirac component c): one complex output
+          const bool left = it < NVL * 4;
+          const int q = left ? it : it - NVL * 4;
+          const int v = q >> 2, c = q & 3;
+          const Real* other = s_adj + (size_t)(left ? sum_r : sum_l) * 8;
+          const int nvo = left ? NVR : NVL;
+          if constexpr (SUMMED) {
+            constexpr int ROW = (1 << H) + (1 << R);
+            const uint16_t* dep = p.dep_tab + (size_t)s * ROW;
+            const unsigned cv = __ldg(dep + (left ? 0 : (1 << H)) + (v >> 1));
+            for (int w = 0; w < nvo; ++w) {
+              const unsigned cw = __ldg(dep + (left ? (1 << H) : 0) + (w >> 1));
+              const int si = left ? (v & 1) : (w & 1), so = left ? (w & 1) : (v & 1);
+              const int lam = si | (so << 1) | (int)((cv | cw) << 2);
+              const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
+              const Real xr = other[w * 8 + 2 * c], xi = other[w * 8 + 2 * c + 1];
+              br[k2] += mr * xr - mi * xi;
+              bi[k2] += mr * xi + mi * xr;
+            }
           } else {
-            const int jt = it - NL * NVL;
-            const int b = jt / NVR, vR = jt - b * NVR;
-            const int so = vR & 1;
-            const unsigned cc = pdep_bits((unsigned)(vR >> 1), SC, N);
-            for (int a = 0; a < NL; ++a)
-              for (int vL = 0; vL < NVL; ++vL) {
-                const int si = vL & 1;
-                const unsigned c = cc | pdep_bits((unsigned)(vL >> 1), S, N);
-                const int lam = si | (so << 1) | (int)(c << 2);
-                const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
-                Real lc[8];
-                load_cur(s_cur, se.leaf_l + a * NVL, NVL, vL, lc);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  acc8[2 * q] += mr * lc[2 * q] - mi * lc[2 * q + 1];
-                  acc8[2 * q + 1] += mr * lc[2 * q + 1] + mi * lc[2 * q];
-                }
-              }
-            store_cur(s_adj, se.leaf_r + b * NVR, NVR, vR, acc8);
+            const Real mr = s_mbar[0], mi = s_mbar[1];
+            const Real xr = other[2 * c], xi = other[2 * c + 1];
+            br[k2] = mr * xr - mi * xi;
+            bi[k2] = mr * xi + mi * xr;
           }
         }
-      } else {
-        const Real mr = s_mbar[0], mi = s_mbar[1];
-        for (int it = lane; it < NL + NR; it += TEAM) {
-          Real acc8[8];
+        team_sync<TEAM>();   // the sums are read; the slots may be overwritten
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc8[c] = (Real)0;
-          const bool left = it < NL;
-          const int cnt = left ? NR : NL;
-          for (int o = 0; o < cnt; ++o) {
-            Real v8[8];
-            load_cur(s_cur, left ? se.leaf_r + o : se.leaf_l + o, 1, 0, v8);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              acc8[2 * q] += mr * v8[2 * q] - mi * v8[2 * q + 1];
-              acc8[2 * q + 1] += mr * v8[2 * q + 1] + mi * v8[2 * q];
-            }
+        for (int k2 = 0; k2 < PER; ++k2) {
+          const int it = lane + k2 * TEAM;
+          if (it >= NITEM) continue;
+          const bool left = it < NVL * 4;
+          const int q = left ? it : it - NVL * 4;
+          const int v = q >> 2, c = q & 3;
+          const int cnt = left ? NL : NR, nv = left ? NVL : NVR;
+          Real* dst = s_adj + (size_t)(left ? se.leaf_l : se.leaf_r) * 8 + v * 8 + 2 * c;
+          for (int a = 0; a < cnt; ++a) {
+            dst[(size_t)a * nv * 8] = br[k2];
+            dst[(size_t)a * nv * 8 + 1] = bi[k2];
           }
-          store_cur(s_adj, left ? se.leaf_l + it : se.leaf_r + (it - NL), 1, 0, acc8);
         }
       }
       team_sync<TEAM>();

@@ -44,6 +44,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_tape);
   cudaFree(p->d_levels);
   cudaFree(p->d_lane_tab);
+  cudaFree(p->d_dep_tab);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
@@ -72,6 +73,7 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.instr = P->d_instr;
   kp.sinstr = P->d_sinstr;
   kp.lane_tab = P->d_lane_tab;
+  kp.dep_tab = P->d_dep_tab;
   kp.phases = P->d_phases;
   kp.sets = P->d_sets;
   if (P->rewrite) {
@@ -297,6 +299,24 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
       }
     }
     if (e == cudaSuccess) e = upload(&P->d_lane_tab, tab);
+    // inverse: the polarisation pattern of each left / right leaf variant
+    const int h = (n + 1) / 2, r = n - h, row = (1 << h) + (1 << r);
+    std::vector<uint16_t> dep(sets.size() * row);
+    for (size_t s = 0; s < sets.size(); ++s) {
+      const unsigned S = sets[s].mask, C = ((1u << n) - 1) & ~S;
+      for (int side = 0; side < 2; ++side) {
+        const unsigned M = side == 0 ? S : C;
+        const int cnt = side == 0 ? (1 << h) : (1 << r);
+        for (int v = 0; v < cnt; ++v) {
+          unsigned d = 0;
+          int o = 0;
+          for (int j = 0; j < n; ++j)
+            if (M & (1u << j)) d |= (((unsigned)v >> o++) & 1u) << j;
+          dep[s * row + (side == 0 ? 0 : (1 << h)) + v] = (uint16_t)d;
+        }
+      }
+    }
+    if (e == cudaSuccess) e = upload(&P->d_dep_tab, dep);
   }
   if (rewrite) {
     if (e == cudaSuccess) e = upload(&P->d_sinstr, P->rsc.instr);

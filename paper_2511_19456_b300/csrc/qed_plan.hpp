@@ -59,7 +59,8 @@ struct qed_plan_s {
   int* d_levels = nullptr;
   RwSchedule rsc;
   SumInstr* d_sinstr = nullptr;
-  uint16_t* d_lane_tab = nullptr;   // spin-summed rewrite plans: leaf variants per (set, lane)
+  uint16_t* d_lane_tab = nullptr;   // spin-summed plans: leaf variants per (set, lane)
+  uint16_t* d_dep_tab = nullptr;    // spin-summed plans: polarisation patterns per (set, leaf variant)
   int device = 0;
   // staging for qed_eval_host
   double* d_stage = nullptr;

@@ -120,6 +120,9 @@ struct KParams {
   // entry [s][c] = pext(c, S) | pext(c, not S) << 8 (left and right leaf
   // variant without the helicity bit)
   const uint16_t* lane_tab;
+  // spin-summed plans: for set s, entries [s][0 .. 2^h) = pdep(v, S) and
+  // [s][2^h .. 2^h + 2^r) = pdep(v, not S) (the adjoint's state index)
+  const uint16_t* dep_tab;
   int ncur;          // stored + local currents
   int ncur_stored;   // currents kept for the whole point
   int team_bytes;
