@@ -40,7 +40,7 @@ PEAK_FP64_TFLOPS = 1.25
 # Version of the forward kernel (arithmetic, shared-memory layout, launch
 # shape); bumped with every change to it.  DRAM traffic recorded in
 # profiles/traffic.json is reported only for the version it was measured on.
-FWD_KERNEL_VERSION = "fwd-5"
+FWD_KERNEL_VERSION = "fwd-6"
 # The same for the kernel of the distributively rewritten DAG.
 RW_KERNEL_VERSION = "rw-2"
 

@@ -135,20 +135,33 @@ QED_HD void pauli_row(const R a[3], const R x[4], R y[4]) {
   y[3] = a[0] * x[1] - a[1] * x[0] - a[2] * x[3];
 }
 
+// -(sigma . a) x and -x (sigma . a): the same products with the sign on the
+// coefficients, so that it costs no separate negation (exact either way).
+template <typename R>
+QED_HD void pauli_col_neg(const R a[3], const R x[4], R y[4]) {
+  y[0] = -a[2] * x[0] - a[0] * x[2] - a[1] * x[3];
+  y[1] = -a[2] * x[1] - a[0] * x[3] + a[1] * x[2];
+  y[2] = -a[0] * x[0] + a[1] * x[1] + a[2] * x[2];
+  y[3] = -a[0] * x[1] - a[1] * x[0] + a[2] * x[3];
+}
+template <typename R>
+QED_HD void pauli_row_neg(const R a[3], const R x[4], R y[4]) {
+  y[0] = -a[2] * x[0] - a[0] * x[2] + a[1] * x[3];
+  y[1] = -a[2] * x[1] - a[0] * x[3] - a[1] * x[2];
+  y[2] = -a[0] * x[0] - a[1] * x[1] + a[2] * x[2];
+  y[3] = -a[0] * x[1] + a[1] * x[0] + a[2] * x[3];
+}
+
 // eps/ = -gamma.eps (eps^0 = 0) = [[0, -s.e], [s.e, 0]]
 template <typename R>
 QED_HD void vertex_col(const R e[3], const R x[8], R y[8]) {
-  R t[4];
-  pauli_col(e, x + 4, t);           // upper = -(s.e) x_lower
-  y[0] = -t[0]; y[1] = -t[1]; y[2] = -t[2]; y[3] = -t[3];
+  pauli_col_neg(e, x + 4, y);       // upper = -(s.e) x_lower
   pauli_col(e, x, y + 4);           // lower = (s.e) x_upper
 }
 template <typename R>
 QED_HD void vertex_row(const R e[3], const R x[8], R y[8]) {
   pauli_row(e, x + 4, y);           // upper = x_lower (s.e)
-  R t[4];
-  pauli_row(e, x, t);               // lower = -x_upper (s.e)
-  y[4] = -t[0]; y[5] = -t[1]; y[6] = -t[2]; y[7] = -t[3];
+  pauli_row_neg(e, x, y + 4);       // lower = -x_upper (s.e)
 }
 
 // (Q/ + m)/D = [[A, -s.q], [s.q, -B]], A = (Q0+m)/D, B = (Q0-m)/D, q = Q/D
