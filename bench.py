@@ -136,9 +136,19 @@ def cpu_baseline(mom: np.ndarray, k: int, target_cpu_s: float = 15.0):
         off += batch
         if dt < 0.5:
             batch *= 2
+    # the same oracle on one thread (the paper times single-threaded code)
+    b1, t1, off1 = max(1, batch // cores), 0.0, off
+    done1 = 0
+    while t1 < 3.0 and off1 + b1 <= len(mom):
+        t0 = time.perf_counter()
+        oracle.m2(mom[off1:off1 + b1], threads=1)
+        t1 += time.perf_counter() - t0
+        done1 += b1
+        off1 += b1
     return {"value": done / t_wall, "unit": "points/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} of the {len(mom)} k={k} points (all states summed), "
-                      f"{t_wall:.1f} s wall on {cores} threads"}
+                      f"{t_wall:.1f} s wall on {cores} threads",
+            "single_thread_points_per_s": done1 / t1 if t1 > 0 else None}
 
 
 def run_reference(args, workload):

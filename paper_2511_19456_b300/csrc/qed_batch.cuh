@@ -18,8 +18,11 @@ struct BatchDesc {
   KParams kp;
 };
 
+// Up to 256 threads per block (the tuner's largest); registers up to 128
+// (FP32) or 255 (FP64) per thread, the range the per-k paths need without
+// spilling.
 template <typename Real>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1)
 qed_batch_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict__ items, int n_items,
                  unsigned* counter) {
   extern __shared__ __align__(16) unsigned char smem[];

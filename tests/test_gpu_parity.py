@@ -163,3 +163,28 @@ def test_plan_info_counts():
     assert info["nodes_unreduced"] == 2183
     assert info["s2_nodes"] == 120 * 128
     assert info["flops_per_point"] > 120 * 128 * 32
+
+
+def test_eval_is_graph_capturable():
+    """qed_eval allocates nothing and does not synchronise: it can be captured
+    in a CUDA graph, and replays give the eager result bit for bit."""
+    k = 4
+    mom = torch.from_numpy(ps.points(k, 5000, 4.0, seed=77)).cuda()
+    for precision in ("fp64", "mixed"):
+        plan = Plan(k, precision=precision)
+        eager = plan.eval(mom)
+        out = torch.empty_like(eager)
+        stream = torch.cuda.Stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(stream):
+            plan.eval(mom, out, stream=stream)   # warm-up on the capture stream
+        torch.cuda.current_stream().wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        out.zero_()
+        with torch.cuda.graph(g):
+            plan.eval(mom, out)
+        for _ in range(2):
+            out.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, eager)
