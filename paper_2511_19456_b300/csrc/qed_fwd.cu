@@ -34,6 +34,16 @@ qed_fwd_kernel(const KParams p) {
                                         smem);
 }
 
+// One fixed state, mixed: 128-thread blocks of up to 128 registers per
+// thread, so that the unrolled rounds of the join do not spill.
+template <int K, int TEAM>
+__global__ void __launch_bounds__(128, 4)
+qed_fwd_fixed_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tpc = blockDim.x / TEAM;
+  eval_range<K, false, float, TEAM, 1>(p, (long long)blockIdx.x * tpc, p.n, (long long)gridDim.x * tpc, smem);
+}
+
 // ----------------------------------------------------------- dispatch
 // Summed spin: one thread keeps all 4 helicity pairs of a polarisation
 // pattern (ES = 1); splitting them over more threads (ES = 2, 4) raises the
@@ -58,12 +68,18 @@ struct KernelChoice {
 
 template <int K, bool SUMMED>
 KernelChoice pick(bool mixed) {
-  if (mixed) {
-    constexpr int T = team_of<K, SUMMED, true>();
-    return {qed_fwd_kernel<K, SUMMED, float, T, es_of<K, SUMMED, true>()>, T};
+  if constexpr (!SUMMED) {
+    constexpr int T = team_of<K, false, false>();
+    if (mixed) return {qed_fwd_fixed_kernel<K, T>, T};
+    return {qed_fwd_kernel<K, false, double, T, 1>, T};
+  } else {
+    if (mixed) {
+      constexpr int T = team_of<K, SUMMED, true>();
+      return {qed_fwd_kernel<K, SUMMED, float, T, es_of<K, SUMMED, true>()>, T};
+    }
+    constexpr int T = team_of<K, SUMMED, false>();
+    return {qed_fwd_kernel<K, SUMMED, double, T, es_of<K, SUMMED, false>()>, T};
   }
-  constexpr int T = team_of<K, SUMMED, false>();
-  return {qed_fwd_kernel<K, SUMMED, double, T, es_of<K, SUMMED, false>()>, T};
 }
 
 KernelChoice forward_kernel(int k, bool summed, bool mixed) {

@@ -408,21 +408,38 @@ __device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab
 #pragma unroll
         for (int i = 0; i < NSI * NSO; ++i) acc[i].commit(ys[i][0], ys[i][1]);
       }
-    } else {
+    } else if constexpr (sizeof(Real) == 8) {
+      // one fixed state, FP64: the lanes split the NL x NR diagrams
       for (int q = lane; q < NL * NR; q += TEAM) {
         const int a = q / NR, b = q - a * NR;
         Real lc[8], rw[8];
         load_cur(s_cur, se.leaf_l + a, 1, 0, lc);
         load_cur(s_cur, se.leaf_r + b, 1, 0, rw);
-        if constexpr (sizeof(Real) == 8) {
-          dot_acc(rw, lc, acc[0].re, acc[0].im);
-        } else {
-          float yr, yi;
-          acc[0].start(yr, yi);
-          dot_acc(rw, lc, yr, yi);
-          acc[0].commit(yr, yi);
+        dot_acc(rw, lc, acc[0].re, acc[0].im);
+      }
+    } else {
+      // one fixed state, mixed: every round of the lanes' split has its own
+      // partial sums (independent FMA chains), added at the end and
+      // committed as one compensated step per set
+      constexpr int ROUNDS = (NL * NR + TEAM - 1) / TEAM;
+      float pr[ROUNDS], pi[ROUNDS];
+#pragma unroll
+      for (int t = 0; t < ROUNDS; ++t) {
+        pr[t] = pi[t] = 0.f;
+        const int q = lane + t * TEAM;
+        if (q < NL * NR) {
+          const int a = q / NR, b = q - a * NR;
+          float lc[8], rw[8];
+          load_cur(s_cur, se.leaf_l + a, 1, 0, lc);
+          load_cur(s_cur, se.leaf_r + b, 1, 0, rw);
+          dot_acc(rw, lc, pr[t], pi[t]);
         }
       }
+#pragma unroll
+      for (int t = 1; t < ROUNDS; ++t) { pr[0] += pr[t]; pi[0] += pi[t]; }
+      float yr, yi;
+      acc[0].start(yr, yi);
+      acc[0].commit(yr + pr[0], yi + pi[0]);
     }
 }
 
