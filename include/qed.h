@@ -324,6 +324,13 @@ qed_status qed_cross_section(qed_plan_t plan, double omega, unsigned long long s
                              double* d_m2, double* d_acc, void* stream, double* sigma, double* sigma_err,
                              double* sum_wm2, double* sum_wm2_sq);
 
+/* Test hook (failure detection without a device fault). Once `after` more
+ * device allocations of the library have succeeded, the next one fails as
+ * if the device were out of memory. The call that made it then returns
+ * QED_ENOMEM and frees what it had allocated. -1 switches the hook off.
+ * QED_EINVAL if after < -1. The paper has no counterpart. */
+qed_status qed_debug_inject_alloc_failure(int after);
+
 const char* qed_status_string(qed_status status);
 
 /* Measured FMA-pipe peak of the current device in TFLOP/s: FP64 for

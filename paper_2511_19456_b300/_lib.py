@@ -79,6 +79,7 @@ SIGNATURES = [
     ("qed_abc_plan_create", ctypes.c_int, [ctypes.POINTER(AbcProcess), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(_vp)]),
     ("qed_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    ("qed_debug_inject_alloc_failure", ctypes.c_int, [ctypes.c_int]),
     ("qed_reduction_steps", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("qed_tape_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(TapeDesc), _vp,
                                        ctypes.POINTER(ctypes.c_int)]),

@@ -182,6 +182,12 @@ class TapePlan(Plan):
         self.mass = float(mass)
 
 
+def inject_alloc_failure(after: int) -> None:
+    """Test hook: after `after` more successful device allocations of the
+    library the next one fails as out of memory (-1 switches it off)."""
+    check(_lib.lib().qed_debug_inject_alloc_failure(int(after)), "qed_debug_inject_alloc_failure")
+
+
 def reduction_steps(k: int) -> int:
     """Single node reductions from the per-diagram CDAG to its fixpoint."""
     out = ctypes.c_int()

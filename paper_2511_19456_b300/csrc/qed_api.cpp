@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -57,6 +58,21 @@ void free_plan(qed_plan_s* p) {
 }
 
 }  // namespace
+
+namespace {
+std::atomic<int> g_alloc_fail_after{-1};   // -1: no injected failure
+}  // namespace
+
+cudaError_t qed::device_alloc(void** p, size_t bytes) {
+  int left = g_alloc_fail_after.load();
+  while (left >= 0) {
+    if (g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 
 qed_status qed::cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return QED_OK;
@@ -114,7 +130,7 @@ namespace {
 template <class T>
 cudaError_t upload(T** dst, const std::vector<T>& src) {
   size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  cudaError_t e = device_alloc((void**)dst, bytes);
   if (e != cudaSuccess) return e;
   if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
@@ -177,6 +193,12 @@ qed_status launch_eval(const qed_plan_s* P, const double* d_mom, long long n, do
 }  // namespace
 
 extern "C" {
+
+qed_status qed_debug_inject_alloc_failure(int after) {
+  if (after < -1) return QED_EINVAL;
+  g_alloc_fail_after.store(after);
+  return QED_OK;
+}
 
 const char* qed_status_string(qed_status s) {
   switch (s) {
@@ -639,7 +661,7 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
     cudaFree(P->d_stage);
     P->d_stage = nullptr;
     P->stage_cap = 0;
-    e = cudaMalloc((void**)&P->d_stage, (size_t)2 * chunk * (stride + 1) * sizeof(double));
+    e = device_alloc((void**)&P->d_stage, (size_t)2 * chunk * (stride + 1) * sizeof(double));
     if (e != cudaSuccess) return cuda_status(e);
     P->stage_cap = chunk;
   }

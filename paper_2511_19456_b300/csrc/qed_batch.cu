@@ -104,7 +104,7 @@ qed_status configure(qed_batch_s* b) {
     cudaFree(b->d_items);
     b->d_items = nullptr;
     b->items_cap = 0;
-    e = cudaMalloc((void**)&b->d_items, b->h_items.size() * sizeof(BatchItem));
+    e = device_alloc((void**)&b->d_items, b->h_items.size() * sizeof(BatchItem));
     if (e != cudaSuccess) return cuda_status(e);
     b->items_cap = b->h_items.size();
   }
@@ -156,8 +156,8 @@ qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long*
   b->mixed = mixed;
   b->h_desc.resize(n_req);
   for (int r = 0; r < n_req; ++r) b->h_desc[r].kp = make_params(plans[r], nullptr, n_points[r], nullptr);
-  cudaError_t e = cudaMalloc((void**)&b->d_desc, n_req * sizeof(BatchDesc));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, 256);
+  cudaError_t e = device_alloc((void**)&b->d_desc, n_req * sizeof(BatchDesc));
+  if (e == cudaSuccess) e = device_alloc((void**)&b->d_counter, 256);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) { free_batch(b); return cuda_status(e); }
   qed_status s = configure(b);

@@ -74,4 +74,7 @@ struct qed_plan_s {
 namespace qed {
 KParams make_params(const qed_plan_s* P, const double* mom, long long n, double* out);
 qed_status cuda_status(cudaError_t e);
+// cudaMalloc behind the library's allocation-failure injection (a host-side
+// fake of an out-of-memory device, for tests: qed_debug_inject_alloc_failure).
+cudaError_t device_alloc(void** p, size_t bytes);
 }  // namespace qed
