@@ -21,13 +21,18 @@ namespace {
 
 // Levels kept for the whole point; deeper levels are rebuilt per photon set.
 // All levels below the leaves fit in shared memory except for spin-summed
-// k = 6, 7, where only the first levels are kept.
-void default_levels(int k, bool summed, int* ls, int* rs) {
+// k = 6, 7, where only the first levels are kept.  One fixed state in the
+// mixed form, k >= 6: one left level fewer.  Its nodes are rebuilt per
+// photon set (+24 % FLOPs at k = 6), but a team's shared memory halves and
+// more teams are resident, which the latency-bound FP32 kernel turns into
+// +12 %; the FP64 kernel, bound by its pipe, keeps all levels.
+void default_levels(int k, bool summed, bool mixed, int* ls, int* rs) {
   const int n = k + 1, h = (n + 1) / 2, r = n - h;
   *ls = h - 1;
   *rs = r - 1;
   if (summed && k == 6) { *ls = 2; *rs = 2; }
   if (summed && k == 7) { *ls = 1; *rs = 1; }
+  if (!summed && mixed && k >= 6) *ls = h - 2;
 }
 
 
@@ -266,7 +271,7 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
     for (int j = 1; j <= k; ++j) P->fixed_pol[j] = spin->hel[j + 2] - 1;
   }
   int ls, rs;
-  default_levels(k, P->summed, &ls, &rs);
+  default_levels(k, P->summed, precision == QED_MIXED, &ls, &rs);
   P->rewrite = rewrite;
   const bool mixed = precision == QED_MIXED;
   P->kc = rewrite ? rewrite_kernel(k, P->summed, mixed) : forward_kernel(k, P->summed, mixed);
@@ -418,7 +423,7 @@ qed_status qed_abc_plan_create(const qed_abc_process* proc, qed_precision precis
   const int n = k + 1;
   try {
     int ls, rs;
-    default_levels(k, false, &ls, &rs);
+    default_levels(k, false, false, &ls, &rs);
     P->sc = build_schedule(k, false, ls, rs);
     if (P->rewrite) P->rsc = build_rewrite_schedule(k, false, rewrite_default_group(k, false, P->kc.team));
   } catch (const std::bad_alloc&) {
@@ -536,7 +541,7 @@ qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* 
   if (e != cudaSuccess) { delete P; return cuda_status(e); }
   try {
     int ls, rs;
-    default_levels(k, false, &ls, &rs);
+    default_levels(k, false, false, &ls, &rs);
     P->sc = build_schedule(k, false, ls, rs);
     P->tp = build_tape(k, reduction_steps);
   } catch (const std::bad_alloc&) {
@@ -717,7 +722,7 @@ qed_status qed_schedule_export(int k, int summed, qed_schedule_desc_t* desc, voi
                                void* phases, void* sets) {
   if (!desc || k < 1 || k > 7) return QED_EINVAL;
   int ls, rs;
-  default_levels(k, summed != 0, &ls, &rs);
+  default_levels(k, summed != 0, false, &ls, &rs);
   Schedule sc;
   try {
     sc = build_schedule(k, summed != 0, ls, rs);
