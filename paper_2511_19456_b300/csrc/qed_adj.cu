@@ -297,8 +297,11 @@ __device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) 
 
 }  // namespace
 
+// Up to 256 threads per block (one team when TEAM > 32); up to 255
+// registers per thread for the spin-summed FP64 form, 128 for the others.
 template <int K, bool SUMMED, typename Real, int TEAM>
-__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256)
+__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256,
+                                  (SUMMED && sizeof(Real) == 8) ? 1 : 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
 qed_adj_kernel(const KParams p) {
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;

@@ -34,6 +34,18 @@ qed_fwd_kernel(const KParams p) {
                                         smem);
 }
 
+// Spin-summed, k other than 4 and 7: launch bounds that allow up to 128
+// registers per thread (the compiler's own choice under the one-argument
+// bounds spilled a few bytes at k = 1, 3, 5, 6; k = 4 and 7 are tuned with
+// those bounds and keep them).
+template <int K, typename Real, int TEAM>
+__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256, 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
+qed_fwd_summed_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tpc = blockDim.x / TEAM;
+  eval_range<K, true, Real, TEAM, 1>(p, (long long)blockIdx.x * tpc, p.n, (long long)gridDim.x * tpc, smem);
+}
+
 // One fixed state, mixed: 128-thread blocks of up to 128 registers per
 // thread, so that the unrolled rounds of the join do not spill.
 template <int K, int TEAM>
@@ -72,6 +84,10 @@ KernelChoice pick(bool mixed) {
     constexpr int T = team_of<K, false, false>();
     if (mixed) return {qed_fwd_fixed_kernel<K, T>, T};
     return {qed_fwd_kernel<K, false, double, T, 1>, T};
+  } else if constexpr (K != 4 && K != 7) {
+    constexpr int T = team_of<K, true, true>();
+    if (mixed) return {qed_fwd_summed_kernel<K, float, T>, T};
+    return {qed_fwd_summed_kernel<K, double, T>, T};
   } else {
     if (mixed) {
       constexpr int T = team_of<K, SUMMED, true>();
