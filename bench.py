@@ -176,8 +176,9 @@ def run_reference(args, workload):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload, "k": w["k"], "n_points": per_step,
-                   "states_summed": 2 ** (w["k"] + 3), "omega": w["omega"],
+        "config": {"workload": workload, "dag": "plain", "k": w["k"], "n_points": w["n_points"],
+                   "omega": w["omega"], "states_summed": 2 ** (w["k"] + 3) if w["summed"] else 1,
+                   "sample_points_per_step": per_step,
                    "note": "each step a bounded sample of the workload on the host cores"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} points per step"},
