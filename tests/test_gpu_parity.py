@@ -188,3 +188,24 @@ def test_eval_is_graph_capturable():
             g.replay()
             torch.cuda.synchronize()
             assert torch.equal(out, eager)
+
+
+def test_concurrent_eval_on_two_streams():
+    """A plan is immutable after creation: evaluations of one plan on two
+    streams at once give the results of serial evaluation."""
+    k = 3
+    plan = Plan(k, precision="mixed")
+    a = torch.from_numpy(ps.points(k, 40000, 3.0, seed=81)).cuda()
+    b = torch.from_numpy(ps.points(k, 30000, 3.0, seed=82)).cuda()
+    ref_a, ref_b = plan.eval(a), plan.eval(b)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    s2.wait_stream(torch.cuda.current_stream())
+    out_a = torch.empty_like(ref_a)
+    out_b = torch.empty_like(ref_b)
+    for _ in range(3):
+        plan.eval(a, out_a, stream=s1)
+        plan.eval(b, out_b, stream=s2)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, ref_a) and torch.equal(out_b, ref_b)
