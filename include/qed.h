@@ -221,6 +221,8 @@ qed_status qed_eval_grad(qed_plan_t plan, const double* d_momenta, long long n,
  * device, evaluates and copies |M|^2 back, chunked so that copies overlap
  * the kernels.  Uses device staging owned by the plan, grown (allocated) on
  * the first call that needs more; synchronises `stream` before returning.
+ * Calls on one plan from several host threads run one at a time (the
+ * staging is the plan's); no copy outlives the call, also on error.
  * Host buffers should be page-locked for full copy bandwidth. */
 qed_status qed_eval_host(qed_plan_t plan, const double* h_momenta, long long n,
                          double* h_out_m2, void* stream);

@@ -657,6 +657,7 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
   if (!P || n < 0) return QED_EINVAL;
   if (n == 0) return QED_OK;
   if (!h_momenta || !h_out_m2) return QED_EINVAL;
+  std::lock_guard<std::mutex> guard(P->stage_lock);   // the staging is the plan's
   cudaStream_t st = (cudaStream_t)stream;
   const long long stride = (long long)(P->k + 3) * 4;
   // two staging buffers of `chunk` points each: momenta then |M|^2
@@ -701,7 +702,12 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
     if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(st, P->ev_d2h[b], 0);
     if (e == cudaSuccess) {
       qed_status s = launch_eval(P, mom_buf[b], m, out_buf[b], st);
-      if (s != QED_OK) return s;
+      if (s != QED_OK) {
+        // let the copies already queued finish with the caller's buffers
+        cudaStreamSynchronize(P->s_h2d);
+        cudaStreamSynchronize(P->s_d2h);
+        return s;
+      }
     }
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_k[b], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_d2h, P->ev_k[b], 0);
@@ -710,6 +716,7 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
                           cudaMemcpyDeviceToHost, P->s_d2h);
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_d2h[b], P->s_d2h);
   }
+  if (e != cudaSuccess) cudaStreamSynchronize(P->s_h2d);   // no copy outlives the call
   if (e == cudaSuccess) e = cudaStreamSynchronize(P->s_d2h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return cuda_status(e);

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "../../include/qed.h"
 #include "dag.hpp"
 #include "qed_types.h"
@@ -62,7 +64,8 @@ struct qed_plan_s {
   uint16_t* d_lane_tab = nullptr;   // spin-summed plans: leaf variants per (set, lane)
   uint16_t* d_dep_tab = nullptr;    // spin-summed plans: polarisation patterns per (set, leaf variant)
   int device = 0;
-  // staging for qed_eval_host
+  // staging for qed_eval_host (one call at a time per plan: stage_lock)
+  std::mutex stage_lock;
   double* d_stage = nullptr;
   long long stage_cap = 0;    // points per buffer
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
