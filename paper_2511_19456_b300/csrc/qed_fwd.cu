@@ -46,6 +46,15 @@ qed_fwd_summed_kernel(const KParams p) {
   eval_range<K, true, Real, TEAM, 1>(p, (long long)blockIdx.x * tpc, p.n, (long long)gridDim.x * tpc, smem);
 }
 
+// One fixed state, FP64: 128-thread blocks of up to 96 registers per thread.
+template <int K, int TEAM>
+__global__ void __launch_bounds__(128, 5)
+qed_fwd_fixed64_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tpc = blockDim.x / TEAM;
+  eval_range<K, false, double, TEAM, 1>(p, (long long)blockIdx.x * tpc, p.n, (long long)gridDim.x * tpc, smem);
+}
+
 // One fixed state, mixed: 128-thread blocks of up to 128 registers per
 // thread, so that the unrolled rounds of the join do not spill.
 template <int K, int TEAM>
@@ -68,6 +77,7 @@ constexpr int es_of() { return 1; }
 template <int K, bool SUMMED, bool MIXED>
 constexpr int team_of() {
   if constexpr (SUMMED) return (1 << (K + 1)) * es_of<K, SUMMED, MIXED>();
+  else if constexpr (!MIXED && K >= 5) return 16;   // FP64: fewer idle lanes in partial rounds
   else return K == 1 ? 2 : (K == 2 ? 4 : (K == 3 ? 8 : (K == 4 ? 16 : 32)));
 }
 
@@ -81,9 +91,10 @@ struct KernelChoice {
 template <int K, bool SUMMED>
 KernelChoice pick(bool mixed) {
   if constexpr (!SUMMED) {
-    constexpr int T = team_of<K, false, false>();
-    if (mixed) return {qed_fwd_fixed_kernel<K, T>, T};
-    return {qed_fwd_kernel<K, false, double, T, 1>, T};
+    constexpr int TM = team_of<K, false, true>();
+    constexpr int TD = team_of<K, false, false>();
+    if (mixed) return {qed_fwd_fixed_kernel<K, TM>, TM};
+    return {qed_fwd_fixed64_kernel<K, TD>, TD};
   } else if constexpr (K != 4 && K != 7) {
     constexpr int T = team_of<K, true, true>();
     if (mixed) return {qed_fwd_summed_kernel<K, float, T>, T};
