@@ -299,7 +299,7 @@ __device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) 
 
 // Up to 256 threads per block (one team when TEAM > 32); up to 255
 // registers per thread for the spin-summed FP64 form, 128 for the others.
-template <int K, bool SUMMED, typename Real, int TEAM>
+template <int K, bool SUMMED, typename Real, int TEAM, bool GMEM>
 __global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256,
                                   (SUMMED && sizeof(Real) == 8) ? 1 : 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
 qed_adj_kernel(const KParams p) {
@@ -315,7 +315,11 @@ qed_adj_kernel(const KParams p) {
   static_assert(!SUMMED || TEAM == (1 << N), "one thread per polarisation pattern");
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const AdjLayout A = adj_layout(K, (int)sizeof(Real), p.ncur, SUMMED);
+  // currents and their adjoints in shared memory, or (GMEM), where they do
+  // not fit, in a global scratch slot of the team; the rest stays in shared
+  // memory.  A separate instance, so that the shared-memory one addresses
+  // its currents as shared memory.
+  const AdjLayout A = adj_layout(K, (int)sizeof(Real), GMEM ? 0 : p.ncur, SUMMED);
   const TeamLayout& L = A.fwd;
   const int lane = threadIdx.x & (TEAM - 1);
   const int team = threadIdx.x / TEAM;
@@ -326,8 +330,16 @@ qed_adj_kernel(const KParams p) {
   Real* s_eps = reinterpret_cast<Real*>(base + L.eps);
   Real* s_spin = reinterpret_cast<Real*>(base + L.spin);
   double* s_red = reinterpret_cast<double*>(base + L.red);
-  Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
-  Real* s_adj = reinterpret_cast<Real*>(base + A.adj);
+  Real* s_cur;
+  Real* s_adj;
+  if constexpr (GMEM) {
+    s_cur = reinterpret_cast<Real*>(static_cast<unsigned char*>(p.adj_scratch) +
+                                    ((size_t)blockIdx.x * tpc + team) * (size_t)p.adj_scratch_team);
+    s_adj = s_cur + (size_t)p.ncur * 8;
+  } else {
+    s_cur = reinterpret_cast<Real*>(base + L.cur);
+    s_adj = reinterpret_cast<Real*>(base + A.adj);
+  }
   Real* s_mbar = reinterpret_cast<Real*>(base + A.mbar);
   double* s_acc_s = reinterpret_cast<double*>(base + A.acc_s);
   double* s_acc_e = reinterpret_cast<double*>(base + A.acc_e);
@@ -551,8 +563,8 @@ constexpr int adj_team() {
 template <int K, bool SUMMED>
 KernelChoice pick_adj(bool mixed) {
   constexpr int T = adj_team<K, SUMMED>();
-  if (mixed) return {qed_adj_kernel<K, SUMMED, float, T>, T};
-  return {qed_adj_kernel<K, SUMMED, double, T>, T};
+  if (mixed) return {qed_adj_kernel<K, SUMMED, float, T, false>, T};
+  return {qed_adj_kernel<K, SUMMED, double, T, false>, T};
 }
 
 KernelChoice adjoint_kernel(int k, bool summed, bool mixed) {
@@ -563,6 +575,15 @@ KernelChoice adjoint_kernel(int k, bool summed, bool mixed) {
     default: return KernelChoice{nullptr, 0};
   }
 #undef QED_CASE
+}
+
+// Global-scratch instances: only the spin-summed FP64 k = 6, 7 adjoints can
+// miss shared memory.
+KernelChoice adjoint_kernel_gmem(int k, bool summed, bool mixed) {
+  if (!summed || mixed) return KernelChoice{nullptr, 0};
+  if (k == 7) return {qed_adj_kernel<7, true, double, adj_team<7, true>(), true>, adj_team<7, true>()};
+  if (k == 6) return {qed_adj_kernel<6, true, double, adj_team<6, true>(), true>, adj_team<6, true>()};
+  return KernelChoice{nullptr, 0};
 }
 
 }  // namespace qed

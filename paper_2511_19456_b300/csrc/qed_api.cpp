@@ -48,6 +48,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_sets_adj);
   cudaFree(p->d_sinstr);
   cudaFree(p->d_tape);
+  cudaFree(p->d_adj_scratch);
   cudaFree(p->d_levels);
   cudaFree(p->d_lane_tab);
   cudaFree(p->d_dep_tab);
@@ -187,6 +188,48 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
     P->grid_adj = per_sm * sms;
     P->has_adj = true;
     return QED_OK;
+  }
+  // nothing fits in shared memory (spin-summed k = 7 in FP64): currents and
+  // adjoints in a global scratch slot per resident team, with the forward
+  // plan's kept levels; the slots stay in the 126 MB L2
+  {
+    int ls, rs;
+    default_levels(k, P->summed, mixed, &ls, &rs);
+    Schedule sc;
+    try {
+      sc = build_schedule(k, P->summed, ls, rs);
+    } catch (const std::bad_alloc&) {
+      return QED_ENOMEM;
+    } catch (...) {
+      return QED_EUNSUPPORTED;
+    }
+    const int ncur = sc.stored_currents + sc.local_currents;
+    const KernelChoice kg = adjoint_kernel_gmem(k, P->summed, mixed);
+    if (!kg.fn || kg.team != team) return QED_OK;
+    AdjLayout A = adj_layout(k, mixed ? 4 : 8, 0, P->summed);
+    const size_t smem = (size_t)(block / team) * A.bytes;
+    if (smem > (size_t)dev_smem) return QED_OK;
+    cudaError_t e = cudaFuncSetAttribute((const void*)kg.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kg.fn, block, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return QED_OK;
+    const long long team_bytes = (long long)ncur * 8 * (mixed ? 4 : 8) * 2;
+    const long long teams = (long long)per_sm * sms * (block / team);
+    e = upload(&P->d_instr_adj, sc.instr);
+    if (e == cudaSuccess) e = upload(&P->d_phases_adj, sc.phases);
+    if (e == cudaSuccess) e = upload(&P->d_sets_adj, sc.sets);
+    if (e == cudaSuccess) e = device_alloc(&P->d_adj_scratch, (size_t)(teams * team_bytes));
+    if (e != cudaSuccess) return cuda_status(e);
+    P->adj_scratch_team = team_bytes;
+    P->kc_adj = kg;
+    P->sc_adj = std::move(sc);
+    P->block_adj = block;
+    P->smem_adj = smem;
+    P->grid_adj = per_sm * sms;
+    P->has_adj = true;
   }
   return QED_OK;
 }
@@ -651,6 +694,8 @@ qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, dou
   kp.n_sets = (int)P->sc_adj.sets.size();
   kp.ncur = P->sc_adj.stored_currents + P->sc_adj.local_currents;
   kp.ncur_stored = P->sc_adj.stored_currents;
+  kp.adj_scratch = P->d_adj_scratch;
+  kp.adj_scratch_team = P->adj_scratch_team;
   const int tpc = P->block_adj / P->kc_adj.team;
   const long long need = (n + tpc - 1) / tpc;
   const int grid = (int)std::min<long long>(need, P->grid_adj);

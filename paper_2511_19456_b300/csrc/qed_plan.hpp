@@ -16,6 +16,7 @@ struct KernelChoice {
 };
 KernelChoice forward_kernel(int k, bool summed, bool mixed);
 KernelChoice adjoint_kernel(int k, bool summed, bool mixed);
+KernelChoice adjoint_kernel_gmem(int k, bool summed, bool mixed);
 KernelChoice rewrite_kernel(int k, bool summed, bool mixed);
 KernelChoice abc_kernel_for(int k, bool mixed, bool rewrite);
 KernelChoice tape_kernel();
@@ -48,6 +49,8 @@ struct qed_plan_s {
   int block_adj = 0, grid_adj = 0;
   size_t smem_adj = 0;
   bool has_adj = false;
+  void* d_adj_scratch = nullptr;     // global currents/adjoints of the adjoint teams
+  long long adj_scratch_team = 0;    // bytes per team
   // distributively rewritten DAG (qed_plan_create_rewrite)
   bool rewrite = false;
   // ABC model (qed_abc_plan_create): scalar currents, A and C masses

@@ -131,6 +131,10 @@ struct KParams {
   double coupling;   // e^(2n); g^(2n) in the ABC model
   int fixed_sin, fixed_sout;       // helicity bit (0: +1, 1: -1)
   unsigned fixed_pol_bits;         // bit j: polarisation of photon j (0: pol 1, 1: pol 2)
+  // adjoint plans whose currents do not fit in shared memory: a global
+  // scratch of adj_scratch_team bytes per team (currents, then adjoints)
+  void* adj_scratch;
+  long long adj_scratch_team;
   // tape plans (node-reduction sweep)
   const TapeInstr* tape;
   const int* tape_levels;          // instruction range of each level
