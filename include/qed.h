@@ -213,7 +213,11 @@ qed_status qed_eval(qed_plan_t plan, const double* d_momenta, long long n,
 
 /* As qed_eval, plus d_grad[N][k][3] = d|M|^2 / d(px, py, pz) of the k
  * outgoing photons (slots 3..k+2), their energies on shell, E_j = |k_j|, and
- * every other momentum held fixed.  d_out_m2 may be NULL. */
+ * every other momentum held fixed.  d_out_m2 may be NULL.  Reverse mode
+ * through the same reduced DAG, sub-currents recomputed per photon set;
+ * where a team's currents and adjoints do not fit in shared memory
+ * (spin-summed k = 7 in FP64), the plan holds a global scratch for them,
+ * allocated at creation.  QED_EUNSUPPORTED for rewrite, ABC and tape plans. */
 qed_status qed_eval_grad(qed_plan_t plan, const double* d_momenta, long long n,
                          double* d_out_m2, double* d_grad, void* stream);
 
