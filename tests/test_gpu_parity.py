@@ -112,19 +112,22 @@ def test_nonfinite_momenta_give_nonfinite_output():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_size_k4_sampled(orc, precision):
     """The 1,048,576-point k = 4 workload in the benchmark's launch
-    configuration, checked on a sample of points against the oracle."""
+    configuration, checked on a 4,096-point sample against the oracle."""
     w = ps.WORKLOADS["compton_k4"]
     mom = ps.workload_points("compton_k4")
     plan = Plan(4, summed=True, precision=precision)
     got = run(plan, mom)
     assert np.all(np.isfinite(got)) and np.all(got > 0)
-    idx = np.random.default_rng(0).choice(w["n_points"], 256, replace=False)
+    # a 4,096-point subset, spread over the whole batch, plus its ends
+    idx = np.random.default_rng(0).choice(w["n_points"], 4096, replace=False)
     idx = np.concatenate([idx, [0, w["n_points"] - 1]])
     ref, kap = orc.m2(mom[idx], kappa=True)
     rel = np.abs(got[idx] / ref - 1.0)
-    print(f"\nfull k=4 {precision}: sampled max rel {rel.max():.3e} median {np.median(rel):.3e}")
+    print(f"\nfull k=4 {precision}: 4,098 sampled points, max rel {rel.max():.3e} median {np.median(rel):.3e}")
     tol = fp64_tol(kap) if precision == "fp64" else mixed_tol(4, kap)
     assert np.all(rel <= tol)
+    if precision == "mixed":
+        assert np.median(rel) <= MIXED_MEDIAN_TOL
 
 
 def test_photon_permutation_invariance_full_size(orc):
