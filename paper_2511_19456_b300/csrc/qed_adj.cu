@@ -26,7 +26,11 @@
 //          df/deps^i = 2 Re e_i, chained through eps_pol(k_j);
 //        finally dE_j/dk_j = k_j / |k_j|.
 // Parameter accumulators are FP64 in shared memory (atomic adds); currents and
-// their adjoints are in the working precision.
+// their adjoints are in the working precision.  One fixed state in mixed
+// precision: the terms of one photon set are first summed in FP32 (one slot
+// per propagator of the set, one per photon), then added to the FP64
+// accumulators once per set; FP64 atomics on words that every lane of the
+// team hits took most of that adjoint's time.
 #include <cuda_runtime.h>
 
 #include "qed_team.cuh"
@@ -167,7 +171,7 @@ template <int TEAM, bool SUMMED, typename Real>
 __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const KParams& p,
                                                const Real* s_q, const Real* s_eps,
                                                const Real* s_spin, const Real* s_cur, Real* s_adj,
-                                               double* s_acc_s, double* s_acc_e) {
+                                               double* s_acc_s, double* s_acc_e, float* s_part) {
 #pragma unroll
   for (int slot = 0; slot < 2; ++slot) {
     const int cnt = ph.cnt[slot];
@@ -250,17 +254,54 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
 #pragma unroll
         for (int c = 0; c < 6; ++c) T.e[c] = (Real)0;
         backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
-        if (in.post) {
+        if (in.post && !(sizeof(Real) == 4 && in.pad)) {
           double* A = s_acc_s + in.post * 10;
 #pragma unroll
           for (int c = 0; c < 10; c += 2) atomic_add_c(A + c, (double)T.s[c], (double)T.s[c + 1]);
         }
-        double* E = s_acc_e + (in.photon * 2 + pol) * 6;
+        if constexpr (sizeof(Real) == 4) {
+          // mixed: FP32 partial sums of the photon set (flush_partials)
+          if (in.pad) {
+            float* A = s_part + (in.pad - 1) * 10;
 #pragma unroll
-        for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T.e[c], (double)T.e[c + 1]);
+            for (int c = 0; c < 10; ++c) atomicAdd(A + c, T.s[c]);
+          }
+          float* E = s_part + p.n_part * 10 + in.photon * 6;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) atomicAdd(E + c, T.e[c]);
+        } else {
+          double* E = s_acc_e + (in.photon * 2 + pol) * 6;
+#pragma unroll
+          for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T.e[c], (double)T.e[c + 1]);
+        }
         if (in.src >= 0) atomic_add_cur(s_adj + (size_t)in.src * 8, 0, xb);
       }
     }
+  }
+}
+
+// Fixed-state mixed adjoint: adds the FP32 partial sums to the FP64
+// accumulators and clears them; set >= 0 flushes that set's propagator
+// slots and the photon terms, set < 0 the photon terms only.  Every slot of
+// a set names a different propagator, so no two lanes add to the same word.
+template <int TEAM, int N>
+__device__ __forceinline__ void flush_partials(const KParams& p, int set, int lane, float* s_part,
+                                               double* s_acc_s, double* s_acc_e) {
+  if (set >= 0) {
+    const uint16_t* tab = p.part_tab + (size_t)set * p.n_part;
+    for (int i = lane; i < p.n_part * 10; i += TEAM) {
+      const int mask = __ldg(tab + i / 10);
+      if (!mask) continue;
+      s_acc_s[mask * 10 + i % 10] += (double)s_part[i];
+      s_part[i] = 0.f;
+    }
+  }
+  float* e = s_part + p.n_part * 10;
+  for (int i = lane; i < N * 6; i += TEAM) {
+    const int j = i / 6;
+    const int pol = (int)((p.fixed_pol_bits >> j) & 1u);
+    s_acc_e[(j * 2 + pol) * 6 + i % 6] += (double)e[i];
+    e[i] = 0.f;
   }
 }
 
@@ -319,7 +360,8 @@ qed_adj_kernel(const KParams p) {
   // not fit, in a global scratch slot of the team; the rest stays in shared
   // memory.  A separate instance, so that the shared-memory one addresses
   // its currents as shared memory.
-  const AdjLayout A = adj_layout(K, (int)sizeof(Real), GMEM ? 0 : p.ncur, SUMMED);
+  constexpr bool PART = !SUMMED && sizeof(Real) == 4;   // FP32 partial sums per photon set
+  const AdjLayout A = adj_layout(K, (int)sizeof(Real), GMEM ? 0 : p.ncur, SUMMED, PART ? p.n_part : 0);
   const TeamLayout& L = A.fwd;
   const int lane = threadIdx.x & (TEAM - 1);
   const int team = threadIdx.x / TEAM;
@@ -344,6 +386,7 @@ qed_adj_kernel(const KParams p) {
   double* s_acc_s = reinterpret_cast<double*>(base + A.acc_s);
   double* s_acc_e = reinterpret_cast<double*>(base + A.acc_e);
   double* s_kbar = reinterpret_cast<double*>(base + A.kbar);
+  float* s_part = reinterpret_cast<float*>(base + A.part);
 
   for (long long pt0 = (long long)blockIdx.x * tpc; pt0 < p.n; pt0 += (long long)gridDim.x * tpc) {
     const long long pt = pt0 + team;
@@ -397,6 +440,8 @@ qed_adj_kernel(const KParams p) {
       for (int i = lane; i < NSUB * 10; i += TEAM) s_acc_s[i] = 0.0;
       for (int i = lane; i < N * 12; i += TEAM) s_acc_e[i] = 0.0;
       for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
+      if constexpr (PART)
+        for (int i = lane; i < p.n_part * 10 + N * 6; i += TEAM) s_part[i] = 0.f;
     }
     team_sync<TEAM>();
 
@@ -482,7 +527,11 @@ qed_adj_kernel(const KParams p) {
       team_sync<TEAM>();
       for (int t = p.n_set_phases - 1; t >= 0; --t) {
         backprop_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + se.phase0 + t), lane, p, s_q, s_eps, s_spin,
-                                           s_cur, s_adj, s_acc_s, s_acc_e);
+                                           s_cur, s_adj, s_acc_s, s_acc_e, s_part);
+        team_sync<TEAM>();
+      }
+      if constexpr (PART) {
+        flush_partials<TEAM, N>(p, s, lane, s_part, s_acc_s, s_acc_e);
         team_sync<TEAM>();
       }
     }
@@ -490,7 +539,11 @@ qed_adj_kernel(const KParams p) {
     // ---- 4. kept inner levels, deepest first
     for (int ph = p.n_stored_phases - 1; ph >= 0; --ph) {
       backprop_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur, s_adj,
-                                         s_acc_s, s_acc_e);
+                                         s_acc_s, s_acc_e, s_part);
+      team_sync<TEAM>();
+    }
+    if constexpr (PART) {
+      flush_partials<TEAM, N>(p, -1, lane, s_part, s_acc_s, s_acc_e);
       team_sync<TEAM>();
     }
 

@@ -52,6 +52,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_levels);
   cudaFree(p->d_lane_tab);
   cudaFree(p->d_dep_tab);
+  cudaFree(p->d_part_tab);
   cudaFree(p->d_stage);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
@@ -145,6 +146,36 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 // The adjoint keeps the forward currents and their adjoints in shared
 // memory: take the deepest kept levels (ls, rs) whose team fits; if none
 // fits, qed_eval_grad reports QED_EUNSUPPORTED for this plan.
+// Fixed-state mixed adjoint: every photon set gets one FP32 partial-sum slot
+// per distinct propagator of its instructions.  Sets the slot (plus one) into
+// the instructions' pad field, fills tab[set][slot] with the propagator's
+// photon set and returns the slots per set.  The kept levels' instructions
+// keep pad = 0 (FP64 accumulation).
+int assign_partial_slots(Schedule& sc, std::vector<uint16_t>* tab) {
+  for (Instr& in : sc.instr) in.pad = 0;
+  std::vector<std::vector<uint16_t>> posts(sc.sets.size());
+  size_t n_part = 1;
+  for (size_t s = 0; s < sc.sets.size(); ++s) {
+    for (int t = 0; t < sc.n_set_phases; ++t) {
+      const Phase& ph = sc.phases[sc.sets[s].phase0 + t];
+      for (int slot = 0; slot < 2; ++slot)
+        for (int i = 0; i < ph.cnt[slot]; ++i) {
+          Instr& in = sc.instr[ph.beg[slot] + i];
+          if (!in.post) continue;
+          auto& v = posts[s];
+          size_t j = std::find(v.begin(), v.end(), in.post) - v.begin();
+          if (j == v.size()) v.push_back(in.post);
+          in.pad = (uint16_t)(j + 1);
+        }
+    }
+    n_part = std::max(n_part, posts[s].size());
+  }
+  tab->assign(sc.sets.size() * n_part, 0);
+  for (size_t s = 0; s < sc.sets.size(); ++s)
+    std::copy(posts[s].begin(), posts[s].end(), tab->begin() + s * n_part);
+  return (int)n_part;
+}
+
 qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
   const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
   P->kc_adj = adjoint_kernel(k, P->summed, mixed);
@@ -168,10 +199,13 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
       return QED_EUNSUPPORTED;
     }
     const int ncur = sc.stored_currents + sc.local_currents;
-    AdjLayout A = adj_layout(k, mixed ? 4 : 8, ncur, P->summed);
+    std::vector<uint16_t> part_tab;
+    const int n_part = (!P->summed && mixed) ? assign_partial_slots(sc, &part_tab) : 0;
+    AdjLayout A = adj_layout(k, mixed ? 4 : 8, ncur, P->summed, n_part);
     const size_t smem = (size_t)(block / team) * A.bytes;
     if (smem > (size_t)dev_smem) continue;
     cudaError_t e = upload(&P->d_instr_adj, sc.instr);
+    if (e == cudaSuccess && n_part > 0) e = upload(&P->d_part_tab, part_tab);
     if (e == cudaSuccess) e = upload(&P->d_phases_adj, sc.phases);
     if (e == cudaSuccess) e = upload(&P->d_sets_adj, sc.sets);
     if (e == cudaSuccess)
@@ -183,6 +217,7 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) return QED_OK;
     P->sc_adj = std::move(sc);
+    P->n_part = n_part;
     P->block_adj = block;
     P->smem_adj = smem;
     P->grid_adj = per_sm * sms;
@@ -696,6 +731,8 @@ qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, dou
   kp.ncur_stored = P->sc_adj.stored_currents;
   kp.adj_scratch = P->d_adj_scratch;
   kp.adj_scratch_team = P->adj_scratch_team;
+  kp.part_tab = P->d_part_tab;
+  kp.n_part = P->n_part;
   const int tpc = P->block_adj / P->kc_adj.team;
   const long long need = (n + tpc - 1) / tpc;
   const int grid = (int)std::min<long long>(need, P->grid_adj);

@@ -87,10 +87,13 @@ QED_HD TapeLayout tape_layout(int k, int n_slots, int n_diag) {
 // polarisation (3 components, complex) parameters and of the photon momenta.
 struct AdjLayout {
   TeamLayout fwd;
-  int adj, mbar, acc_s, acc_e, kbar, bytes;
+  int adj, mbar, acc_s, acc_e, kbar, part, bytes;
 };
 
-QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed) {
+// n_part > 0 (one fixed state, mixed): FP32 partial sums of one photon set's
+// parameter terms, n_part propagator slots of 10 reals and 6 reals per
+// photon, added to the FP64 accumulators once per set.
+QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_part = 0) {
   const int n = k + 1;
   AdjLayout A;
   A.fwd = team_layout(k, real_size, ncur);
@@ -100,6 +103,7 @@ QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed) {
   A.acc_s = off; off = align16(off + (1 << n) * 10 * 8);
   A.acc_e = off; off = align16(off + n * 2 * 6 * 8);
   A.kbar = off;  off = align16(off + n * 4 * 8);
+  A.part = off;  off = align16(off + (n_part > 0 ? (n_part * 10 + n * 6) * 4 : 0));
   A.bytes = off;
   return A;
 }
@@ -135,6 +139,11 @@ struct KParams {
   // scratch of adj_scratch_team bytes per team (currents, then adjoints)
   void* adj_scratch;
   long long adj_scratch_team;
+  // fixed-state mixed adjoint: for set s, entry [s][i] is the propagator
+  // photon set of partial-sum slot i (0: unused); an instruction of the set
+  // names its slot as pad - 1 (pad = 0: no slot, direct FP64 accumulation)
+  const uint16_t* part_tab;
+  int n_part;
   // tape plans (node-reduction sweep)
   const TapeInstr* tape;
   const int* tape_levels;          // instruction range of each level

@@ -79,6 +79,24 @@ def test_mixed_adjoint_close_to_fp64(orc):
     assert err.max() < 1e-3
 
 
+@pytest.mark.parametrize("k,npts", [(2, 64), (3, 64), (4, 32), (5, 16), (6, 64)])
+def test_fixed_state_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
+    """One fixed spin state, mixed precision: FP32 currents, adjoints and
+    parameter terms, with the terms of one photon set summed in FP32 before
+    they are added to the FP64 accumulators.  Bound per point, relative to
+    max|g_ref|: the forward mixed bound 32 (2n - 1) u32 max(kappa, 1)."""
+    from tests.test_gpu_parity import mixed_tol
+    mom = ps.points(k, npts, 1.0 + k, seed=630 + k)
+    hel = fixed_hel(k)
+    _, g = gpu_grad(Plan(k, summed=False, hel=hel, precision="mixed"), mom)
+    _, ref_g = orc.grad(mom, sum_mask=0, hel=hel)
+    _, kap = orc.m2(mom, sum_mask=0, hel=hel, kappa=True)
+    err = np.abs(g - ref_g).max(axis=(1, 2)) / np.abs(ref_g).max(axis=(1, 2))
+    print(f"\nfixed mixed adjoint k={k}: grad max rel err {err.max():.3e} median {np.median(err):.3e} "
+          f"(kappa max {kap.max():.1f})")
+    assert np.all(err <= mixed_tol(k, kap)), (err.max(), int(err.argmax()))
+
+
 def test_autograd_function():
     from paper_2511_19456_b300.autograd import m2
     k = 3
