@@ -25,8 +25,9 @@
 //        vertex of photon j (eps/ = -gamma^i eps^i): with e_i = -wbar gamma^i x,
 //          df/deps^i = 2 Re e_i, chained through eps_pol(k_j);
 //        finally dE_j/dk_j = k_j / |k_j|.
-// Parameter accumulators are FP64 in shared memory (atomic adds); currents and
-// their adjoints are in the working precision.  One fixed state in mixed
+// Q, D and eps are real, so only the real parts of s_mu, u and e_i are
+// accumulated.  The accumulators are FP64 in shared memory (atomic adds);
+// currents and their adjoints are in the working precision.  One fixed state in mixed
 // precision: the terms of one photon set are first summed in FP32 (one slot
 // per propagator of the set, one per photon), then added to the FP64
 // accumulators once per set; FP64 atomics on words that every lane of the
@@ -78,11 +79,6 @@ __device__ __forceinline__ void bilinears(const Real* a, const Real* b, Cf<Real>
           ab[0][2].im - ab[1][3].im - ab[2][0].im + ab[3][1].im};
 }
 
-__device__ __forceinline__ void atomic_add_c(double* p, double re, double im) {
-  atomicAdd(p, re);
-  atomicAdd(p + 1, im);
-}
-
 template <typename Real>
 __device__ __forceinline__ void atomic_add_cur(Real* p, int nv, const Real x[8]) {
   typedef typename C2<Real>::T T;
@@ -94,11 +90,12 @@ __device__ __forceinline__ void atomic_add_cur(Real* p, int nv, const Real x[8])
 
 // Parameter terms of one instruction output: the propagator bilinears
 // (s_mu, mu = 0..3, and u) of its post set and the polarisation terms e_i
-// (i = 1..3) of its photon, in the working precision.
+// (i = 1..3) of its photon, in the working precision.  Q, D and eps are
+// real, so df = 2 Re(...) needs only their real parts.
 template <typename Real>
 struct ParTerms {
-  Real s[10];   // s_0..s_3, u (complex)
-  Real e[6];    // e_1..e_3 (complex), already with the sign of eps/ = -gamma.eps
+  Real s[5];    // Re s_0..s_3, Re u
+  Real e[3];    // Re e_1..e_3, already with the sign of eps/ = -gamma.eps
 };
 
 // One instruction output variant (polarisation pol): given its adjoint ybar
@@ -123,9 +120,8 @@ __device__ __forceinline__ void backprop_terms(const Instr& in, int pol, const R
       Cf<Real> u2, sd[4];
       bilinears(yb, y, sd, u2);                 // u = ybar . y
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) { T.s[2 * mu] += s[mu].re; T.s[2 * mu + 1] += s[mu].im; }
-      T.s[8] += u2.re;
-      T.s[9] += u2.im;
+      for (int mu = 0; mu < 4; ++mu) T.s[mu] += s[mu].re;
+      T.s[4] += u2.re;
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
@@ -143,9 +139,8 @@ __device__ __forceinline__ void backprop_terms(const Instr& in, int pol, const R
       Cf<Real> u2, sd[4];
       bilinears(y, yb, sd, u2);                 // u = y . ybar
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) { T.s[2 * mu] += s[mu].re; T.s[2 * mu + 1] += s[mu].im; }
-      T.s[8] += u2.re;
-      T.s[9] += u2.im;
+      for (int mu = 0; mu < 4; ++mu) T.s[mu] += s[mu].re;
+      T.s[4] += u2.re;
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
@@ -156,7 +151,7 @@ __device__ __forceinline__ void backprop_terms(const Instr& in, int pol, const R
 #pragma unroll
   for (int i = 0; i < 8; ++i) xbar[i] += t[i];
 #pragma unroll
-  for (int i = 1; i < 4; ++i) { T.e[2 * (i - 1)] -= s[i].re; T.e[2 * (i - 1) + 1] -= s[i].im; }
+  for (int i = 1; i < 4; ++i) T.e[i - 1] -= s[i].re;
 }
 
 // Reverse of one phase: every instruction passes its outputs' adjoints to its
@@ -192,9 +187,9 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
 #pragma unroll
-          for (int c = 0; c < 10; ++c) T[q].s[c] = (Real)0;
+          for (int c = 0; c < 5; ++c) T[q].s[c] = (Real)0;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) T[q].e[c] = (Real)0;
+          for (int c = 0; c < 3; ++c) T[q].e[c] = (Real)0;
         }
         if (valid) {
           Real x[8], xb[8], yb[8];
@@ -215,26 +210,26 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
         }
         // the propagator terms do not depend on the polarisation
 #pragma unroll
-        for (int c = 0; c < 10; ++c) T[0].s[c] += T[1].s[c];
+        for (int c = 0; c < 5; ++c) T[0].s[c] += T[1].s[c];
         for (int off = 1; off < G; off <<= 1) {
 #pragma unroll
-          for (int c = 0; c < 10; ++c) T[0].s[c] += __shfl_xor_sync(0xffffffffu, T[0].s[c], off);
+          for (int c = 0; c < 5; ++c) T[0].s[c] += __shfl_xor_sync(0xffffffffu, T[0].s[c], off);
 #pragma unroll
           for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int c = 0; c < 6; ++c) T[q].e[c] += __shfl_xor_sync(0xffffffffu, T[q].e[c], off);
+            for (int c = 0; c < 3; ++c) T[q].e[c] += __shfl_xor_sync(0xffffffffu, T[q].e[c], off);
         }
         if (valid && (vp & (G - 1)) == 0) {
           if (in.post) {
-            double* A = s_acc_s + in.post * 10;
+            double* A = s_acc_s + in.post * 5;
 #pragma unroll
-            for (int c = 0; c < 10; c += 2) atomic_add_c(A + c, (double)T[0].s[c], (double)T[0].s[c + 1]);
+            for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T[0].s[c]);
           }
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            double* E = s_acc_e + (in.photon * 2 + q) * 6;
+            double* E = s_acc_e + (in.photon * 2 + q) * 3;
 #pragma unroll
-            for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T[q].e[c], (double)T[q].e[c + 1]);
+            for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T[q].e[c]);
           }
         }
       }
@@ -250,29 +245,29 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
         load_cur(s_adj, in.dst, 1, 0, yb);
         ParTerms<Real> T;
 #pragma unroll
-        for (int c = 0; c < 10; ++c) T.s[c] = (Real)0;
+        for (int c = 0; c < 5; ++c) T.s[c] = (Real)0;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) T.e[c] = (Real)0;
+        for (int c = 0; c < 3; ++c) T.e[c] = (Real)0;
         backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
         if (in.post && !(sizeof(Real) == 4 && in.pad)) {
-          double* A = s_acc_s + in.post * 10;
+          double* A = s_acc_s + in.post * 5;
 #pragma unroll
-          for (int c = 0; c < 10; c += 2) atomic_add_c(A + c, (double)T.s[c], (double)T.s[c + 1]);
+          for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T.s[c]);
         }
         if constexpr (sizeof(Real) == 4) {
           // mixed: FP32 partial sums of the photon set (flush_partials)
           if (in.pad) {
-            float* A = s_part + (in.pad - 1) * 10;
+            float* A = s_part + (in.pad - 1) * 5;
 #pragma unroll
-            for (int c = 0; c < 10; ++c) atomicAdd(A + c, T.s[c]);
+            for (int c = 0; c < 5; ++c) atomicAdd(A + c, T.s[c]);
           }
-          float* E = s_part + p.n_part * 10 + in.photon * 6;
+          float* E = s_part + p.n_part * 5 + in.photon * 3;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) atomicAdd(E + c, T.e[c]);
+          for (int c = 0; c < 3; ++c) atomicAdd(E + c, T.e[c]);
         } else {
-          double* E = s_acc_e + (in.photon * 2 + pol) * 6;
+          double* E = s_acc_e + (in.photon * 2 + pol) * 3;
 #pragma unroll
-          for (int c = 0; c < 6; c += 2) atomic_add_c(E + c, (double)T.e[c], (double)T.e[c + 1]);
+          for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T.e[c]);
         }
         if (in.src >= 0) atomic_add_cur(s_adj + (size_t)in.src * 8, 0, xb);
       }
@@ -289,18 +284,18 @@ __device__ __forceinline__ void flush_partials(const KParams& p, int set, int la
                                                double* s_acc_s, double* s_acc_e) {
   if (set >= 0) {
     const uint16_t* tab = p.part_tab + (size_t)set * p.n_part;
-    for (int i = lane; i < p.n_part * 10; i += TEAM) {
-      const int mask = __ldg(tab + i / 10);
+    for (int i = lane; i < p.n_part * 5; i += TEAM) {
+      const int mask = __ldg(tab + i / 5);
       if (!mask) continue;
-      s_acc_s[mask * 10 + i % 10] += (double)s_part[i];
+      s_acc_s[mask * 5 + i % 5] += (double)s_part[i];
       s_part[i] = 0.f;
     }
   }
-  float* e = s_part + p.n_part * 10;
-  for (int i = lane; i < N * 6; i += TEAM) {
-    const int j = i / 6;
+  float* e = s_part + p.n_part * 5;
+  for (int i = lane; i < N * 3; i += TEAM) {
+    const int j = i / 3;
     const int pol = (int)((p.fixed_pol_bits >> j) & 1u);
-    s_acc_e[(j * 2 + pol) * 6 + i % 6] += (double)e[i];
+    s_acc_e[(j * 2 + pol) * 3 + i % 3] += (double)e[i];
     e[i] = 0.f;
   }
 }
@@ -437,11 +432,11 @@ qed_adj_kernel(const KParams p) {
     {
       const int nst = p.ncur_stored * 8;
       for (int i = lane; i < nst; i += TEAM) s_adj[i] = (Real)0;
-      for (int i = lane; i < NSUB * 10; i += TEAM) s_acc_s[i] = 0.0;
-      for (int i = lane; i < N * 12; i += TEAM) s_acc_e[i] = 0.0;
+      for (int i = lane; i < NSUB * 5; i += TEAM) s_acc_s[i] = 0.0;
+      for (int i = lane; i < N * 6; i += TEAM) s_acc_e[i] = 0.0;
       for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
       if constexpr (PART)
-        for (int i = lane; i < p.n_part * 10 + N * 6; i += TEAM) s_part[i] = 0.f;
+        for (int i = lane; i < p.n_part * 5 + N * 3; i += TEAM) s_part[i] = 0.f;
     }
     team_sync<TEAM>();
 
@@ -562,13 +557,13 @@ qed_adj_kernel(const KParams p) {
       D = __dsub_rn(D, __dmul_rn(q2, q2));
       D = __dsub_rn(D, __dmul_rn(q3, q3));
       D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
-      const double* Ac = s_acc_s + mask * 10;
+      const double* Ac = s_acc_s + mask * 5;
       const double Q[4] = {q0, q1, q2, q3};
       double qb[4];
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
         const double eta = mu == 0 ? 1.0 : -1.0;
-        qb[mu] = 2.0 * eta * (Ac[2 * mu] - 2.0 * Q[mu] * Ac[8]) / D;   // real part
+        qb[mu] = 2.0 * eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) / D;
       }
       for (int j = 1; j < N; ++j)
         if (mask & (1 << j))
@@ -578,12 +573,12 @@ qed_adj_kernel(const KParams p) {
     for (int it = lane; it < 2 * N; it += TEAM) {
       const int j = it >> 1, pb = it & 1;
       if (j == 0) continue;
-      const double* E = s_acc_e + (j * 2 + pb) * 6;
+      const double* E = s_acc_e + (j * 2 + pb) * 3;
       double d[3][3];
       dpol(s_mom + 4 * (j + 2), pb, d);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const double g = 2.0 * (E[0] * d[a][0] + E[2] * d[a][1] + E[4] * d[a][2]);
+        const double g = 2.0 * (E[0] * d[a][0] + E[1] * d[a][1] + E[2] * d[a][2]);
         atomicAdd(s_kbar + 4 * j + 1 + a, g);
       }
     }

@@ -90,8 +90,10 @@ struct AdjLayout {
   int adj, mbar, acc_s, acc_e, kbar, part, bytes;
 };
 
+// Parameter accumulators: the real parts of 5 propagator terms per photon
+// subset and of 3 polarisation terms per photon and polarisation.
 // n_part > 0 (one fixed state, mixed): FP32 partial sums of one photon set's
-// parameter terms, n_part propagator slots of 10 reals and 6 reals per
+// parameter terms, n_part propagator slots of 5 reals and 3 reals per
 // photon, added to the FP64 accumulators once per set.
 QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_part = 0) {
   const int n = k + 1;
@@ -100,10 +102,10 @@ QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_p
   int off = A.fwd.bytes;
   A.adj = off;   off = align16(off + ncur * 8 * real_size);
   A.mbar = off;  off = align16(off + (summed ? (1 << (n + 2)) : 1) * 2 * real_size);
-  A.acc_s = off; off = align16(off + (1 << n) * 10 * 8);
-  A.acc_e = off; off = align16(off + n * 2 * 6 * 8);
+  A.acc_s = off; off = align16(off + (1 << n) * 5 * 8);
+  A.acc_e = off; off = align16(off + n * 2 * 3 * 8);
   A.kbar = off;  off = align16(off + n * 4 * 8);
-  A.part = off;  off = align16(off + (n_part > 0 ? (n_part * 10 + n * 6) * 4 : 0));
+  A.part = off;  off = align16(off + (n_part > 0 ? (n_part * 5 + n * 3) * 4 : 0));
   A.bytes = off;
   return A;
 }
