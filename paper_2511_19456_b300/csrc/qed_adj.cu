@@ -167,11 +167,51 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
                                                const Real* s_q, const Real* s_eps,
                                                const Real* s_spin, const Real* s_cur, Real* s_adj,
                                                double* s_acc_s, double* s_acc_e, float* s_part) {
+  if constexpr (!SUMMED) {
+    // one fixed state: both ranges in one loop (as in run_phase)
+    const int c0 = ph.cnt[0], total = c0 + ph.cnt[1];
+    for (int it = lane; it < total; it += TEAM) {
+      const Instr in = ld_instr(p.instr + (it < c0 ? ph.beg[0] + it : ph.beg[1] + (it - c0)));
+      const int pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
+      Real x[8], xb[8], yb[8];
 #pragma unroll
-  for (int slot = 0; slot < 2; ++slot) {
-    const int cnt = ph.cnt[slot];
-    if (cnt == 0) continue;
-    if constexpr (SUMMED) {
+      for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
+      if (in.src < 0) load8(s_spin + (in.side * 2 + (in.side == 0 ? p.fixed_sin : p.fixed_sout)) * 8, x);
+      else load_cur(s_cur, in.src, 1, 0, x);
+      load_cur(s_adj, in.dst, 1, 0, yb);
+      ParTerms<Real> T;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) T.s[c] = (Real)0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) T.e[c] = (Real)0;
+      backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
+      if (in.post && !(sizeof(Real) == 4 && in.pad)) {
+        double* A = s_acc_s + in.post * 5;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T.s[c]);
+      }
+      if constexpr (sizeof(Real) == 4) {
+        // mixed: FP32 partial sums of the photon set (flush_partials)
+        if (in.pad) {
+          float* A = s_part + (in.pad - 1) * 5;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) atomicAdd(A + c, T.s[c]);
+        }
+        float* E = s_part + p.n_part * 5 + in.photon * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(E + c, T.e[c]);
+      } else {
+        double* E = s_acc_e + (in.photon * 2 + pol) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T.e[c]);
+      }
+      if (in.src >= 0) atomic_add_cur(s_adj + (size_t)in.src * 8, 0, xb);
+    }
+  } else {
+#pragma unroll
+    for (int slot = 0; slot < 2; ++slot) {
+      const int cnt = ph.cnt[slot];
+      if (cnt == 0) continue;
       constexpr int WMAX = TEAM < 32 ? TEAM : 32;
       const int lg = ph.level[slot];
       const int total = cnt << lg;
@@ -232,44 +272,6 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
             for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T[q].e[c]);
           }
         }
-      }
-    } else {
-      for (int it = lane; it < cnt; it += TEAM) {
-        const Instr in = ld_instr(p.instr + ph.beg[slot] + it);
-        const int pol = (int)((p.fixed_pol_bits >> in.photon) & 1u);
-        Real x[8], xb[8], yb[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) xb[c] = (Real)0;
-        if (in.src < 0) load8(s_spin + (in.side * 2 + (in.side == 0 ? p.fixed_sin : p.fixed_sout)) * 8, x);
-        else load_cur(s_cur, in.src, 1, 0, x);
-        load_cur(s_adj, in.dst, 1, 0, yb);
-        ParTerms<Real> T;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) T.s[c] = (Real)0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) T.e[c] = (Real)0;
-        backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
-        if (in.post && !(sizeof(Real) == 4 && in.pad)) {
-          double* A = s_acc_s + in.post * 5;
-#pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T.s[c]);
-        }
-        if constexpr (sizeof(Real) == 4) {
-          // mixed: FP32 partial sums of the photon set (flush_partials)
-          if (in.pad) {
-            float* A = s_part + (in.pad - 1) * 5;
-#pragma unroll
-            for (int c = 0; c < 5; ++c) atomicAdd(A + c, T.s[c]);
-          }
-          float* E = s_part + p.n_part * 5 + in.photon * 3;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) atomicAdd(E + c, T.e[c]);
-        } else {
-          double* E = s_acc_e + (in.photon * 2 + pol) * 3;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T.e[c]);
-        }
-        if (in.src >= 0) atomic_add_cur(s_adj + (size_t)in.src * 8, 0, xb);
       }
     }
   }

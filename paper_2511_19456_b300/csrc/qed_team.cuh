@@ -127,17 +127,27 @@ template <int TEAM, bool SUMMED, typename Real>
 __device__ __forceinline__ void run_phase(const Phase& ph, int lane, const KParams& p,
                                           const Real* s_q, const Real* s_eps,
                                           const Real* s_spin, Real* s_cur) {
-#pragma unroll
-  for (int slot = 0; slot < 2; ++slot) {
-    const int cnt = ph.cnt[slot];
-    if (cnt == 0) continue;
-    const int lg = SUMMED ? ph.level[slot] + 1 : 0;
-    const int total = cnt << lg;
+  if constexpr (!SUMMED) {
+    // one fixed state: one item per instruction, both ranges in one loop,
+    // so that the short range does not take a round of mostly idle lanes
+    const int c0 = ph.cnt[0], total = c0 + ph.cnt[1];
     for (int it = lane; it < total; it += TEAM) {
-      const int i = it >> lg;
-      const int v = it & ((1 << lg) - 1);
-      const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
-      apply_instr<SUMMED, Real>(in, v, p, s_q, s_eps, s_spin, s_cur);
+      const int idx = it < c0 ? ph.beg[0] + it : ph.beg[1] + (it - c0);
+      apply_instr<false, Real>(ld_instr(p.instr + idx), 0, p, s_q, s_eps, s_spin, s_cur);
+    }
+  } else {
+#pragma unroll
+    for (int slot = 0; slot < 2; ++slot) {
+      const int cnt = ph.cnt[slot];
+      if (cnt == 0) continue;
+      const int lg = ph.level[slot] + 1;
+      const int total = cnt << lg;
+      for (int it = lane; it < total; it += TEAM) {
+        const int i = it >> lg;
+        const int v = it & ((1 << lg) - 1);
+        const Instr in = ld_instr(p.instr + ph.beg[slot] + i);
+        apply_instr<true, Real>(in, v, p, s_q, s_eps, s_spin, s_cur);
+      }
     }
   }
 }
