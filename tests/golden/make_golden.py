@@ -20,7 +20,7 @@ K7_FILE = os.path.join(HERE, "k7_summed_oracle.txt")
 
 def main():
     w = ps.WORKLOADS["compton_k7"]
-    n = 64
+    n = 512
     mom = ps.points(w["k"], n, w["omega"], w["seed"] + 17)
     m2, kap = oracle.m2(mom, kappa=True)
     with open(K7_FILE, "w") as f:
