@@ -40,43 +40,49 @@ namespace qed {
 
 namespace {
 
+// Real parts of the bilinears s_mu = sum_ab a_a gamma^mu_ab b_b (mu = 0..3,
+// Dirac representation) and u = sum_c a_c b_c, for complex 4-vectors a, b
+// stored as 8 reals.  Q, D and eps are real, so df = 2 Re(...) needs only
+// these.  Each is one FMA chain over its four products:
+//   gamma^0 = diag(1, 1, -1, -1):             s_0 = a0 b0 + a1 b1 - a2 b2 - a3 b3
+//   gamma^i = [[0, sigma^i], [-sigma^i, 0]]:  s_i = a_u sigma^i b_l - a_l sigma^i b_u
+//     x sigma^1 y = x0 y1 + x1 y0   ->  s_1 = a0 b3 + a1 b2 - a2 b1 - a3 b0
+//     x sigma^2 y = i (x1 y0 - x0 y1) -> Re s_2 = Im(a0 b3 - a1 b2 + a3 b0 - a2 b1)
+//     x sigma^3 y = x0 y0 - x1 y1   ->  s_3 = a0 b2 - a1 b3 - a2 b0 + a3 b1
+// acc + g Re(a_i b_j) and acc + g Im(a_i b_j), g = +-1
 template <typename Real>
-struct Cf {
-  Real re, im;
-};
-
+__device__ __forceinline__ Real fre(const Real* a, int i, const Real* b, int j, Real g, Real acc) {
+  return fma(g * a[2 * i], b[2 * j], fma(-g * a[2 * i + 1], b[2 * j + 1], acc));
+}
 template <typename Real>
-__device__ __forceinline__ Cf<Real> cmul(Real ar, Real ai, Real br, Real bi) {
-  return {ar * br - ai * bi, ar * bi + ai * br};
+__device__ __forceinline__ Real fim(const Real* a, int i, const Real* b, int j, Real g, Real acc) {
+  return fma(g * a[2 * i], b[2 * j + 1], fma(g * a[2 * i + 1], b[2 * j], acc));
 }
 
-// s_mu = sum_ab a_a gamma^mu_ab b_b (mu = 0..3, Dirac representation) and
-// u = sum_c a_c b_c, for complex 4-vectors a, b stored as 8 reals.
 template <typename Real>
-__device__ __forceinline__ void bilinears(const Real* a, const Real* b, Cf<Real> s[4], Cf<Real>& u) {
-  Cf<Real> ab[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) ab[i][j] = cmul(a[2 * i], a[2 * i + 1], b[2 * j], b[2 * j + 1]);
-  // gamma^0 = diag(1, 1, -1, -1)
-  s[0] = {ab[0][0].re + ab[1][1].re - ab[2][2].re - ab[3][3].re,
-          ab[0][0].im + ab[1][1].im - ab[2][2].im - ab[3][3].im};
-  u = {ab[0][0].re + ab[1][1].re + ab[2][2].re + ab[3][3].re,
-       ab[0][0].im + ab[1][1].im + ab[2][2].im + ab[3][3].im};
-  // gamma^i = [[0, sigma^i], [-sigma^i, 0]]:  a_u sigma^i b_l - a_l sigma^i b_u
-  // x sigma^1 y = x0 y1 + x1 y0
-  s[1] = {ab[0][3].re + ab[1][2].re - ab[2][1].re - ab[3][0].re,
-          ab[0][3].im + ab[1][2].im - ab[2][1].im - ab[3][0].im};
-  // x sigma^2 y = i (x1 y0 - x0 y1)
-  {
-    const Real tr = (ab[1][2].re - ab[0][3].re) - (ab[3][0].re - ab[2][1].re);
-    const Real ti = (ab[1][2].im - ab[0][3].im) - (ab[3][0].im - ab[2][1].im);
-    s[2] = {-ti, tr};
-  }
-  // x sigma^3 y = x0 y0 - x1 y1
-  s[3] = {ab[0][2].re - ab[1][3].re - ab[2][0].re + ab[3][1].re,
-          ab[0][2].im - ab[1][3].im - ab[2][0].im + ab[3][1].im};
+__device__ __forceinline__ Real bil_s0(const Real* a, const Real* b) {
+  const Real one = 1, mone = -1;
+  return fre(a, 3, b, 3, mone, fre(a, 2, b, 2, mone, fre(a, 1, b, 1, one, fre(a, 0, b, 0, one, (Real)0))));
+}
+template <typename Real>
+__device__ __forceinline__ Real bil_s1(const Real* a, const Real* b) {
+  const Real one = 1, mone = -1;
+  return fre(a, 3, b, 0, mone, fre(a, 2, b, 1, mone, fre(a, 1, b, 2, one, fre(a, 0, b, 3, one, (Real)0))));
+}
+template <typename Real>
+__device__ __forceinline__ Real bil_s2(const Real* a, const Real* b) {
+  const Real one = 1, mone = -1;
+  return fim(a, 2, b, 1, mone, fim(a, 3, b, 0, one, fim(a, 1, b, 2, mone, fim(a, 0, b, 3, one, (Real)0))));
+}
+template <typename Real>
+__device__ __forceinline__ Real bil_s3(const Real* a, const Real* b) {
+  const Real one = 1, mone = -1;
+  return fre(a, 3, b, 1, one, fre(a, 2, b, 0, mone, fre(a, 1, b, 3, mone, fre(a, 0, b, 2, one, (Real)0))));
+}
+template <typename Real>
+__device__ __forceinline__ Real bil_u(const Real* a, const Real* b) {
+  const Real one = 1;
+  return fre(a, 3, b, 3, one, fre(a, 2, b, 2, one, fre(a, 1, b, 1, one, fre(a, 0, b, 0, one, (Real)0))));
 }
 
 template <typename Real>
@@ -98,60 +104,56 @@ struct ParTerms {
   Real e[3];    // Re e_1..e_3, already with the sign of eps/ = -gamma.eps
 };
 
-// One instruction output variant (polarisation pol): given its adjoint ybar
-// and its input x, add the parameter terms to T and the input's adjoint
-// contribution to xbar.
+// One instruction output variant (polarisation pol): given its adjoint ybar,
+// its input x and (when it has a propagator) its output y = P eps/ x as
+// stored by the forward pass, add the parameter terms to T and the input's
+// adjoint contribution to xbar.
 template <typename Real>
 __device__ __forceinline__ void backprop_terms(const Instr& in, int pol, const Real x[8], const Real yb[8],
-                                               const Real* s_q, const Real* s_eps, ParTerms<Real>& T,
-                                               Real xbar[8]) {
+                                               const Real y[8], const Real* s_q, const Real* s_eps,
+                                               ParTerms<Real>& T, Real xbar[8]) {
   const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
   const Real ev[3] = {e3[0], e3[1], e3[2]};
   Real w[8], wb[8], t[8];
-  Cf<Real> s[4], u;
   if (in.side == 0) {
     vertex_col(ev, x, w);                       // w = eps/ x
     if (in.post) {
       const Real* P = s_q + in.post * 5;
-      Real y[8];
-      prop_col(P, w, y);                        // y = P w
       prop_row(P, yb, wb);                      // wbar = ybar P
-      bilinears(yb, w, s, u);                   // s_mu = ybar g^mu w
-      Cf<Real> u2, sd[4];
-      bilinears(yb, y, sd, u2);                 // u = ybar . y
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) T.s[mu] += s[mu].re;
-      T.s[4] += u2.re;
+      T.s[0] += bil_s0(yb, w);                  // s_mu = ybar g^mu w
+      T.s[1] += bil_s1(yb, w);
+      T.s[2] += bil_s2(yb, w);
+      T.s[3] += bil_s3(yb, w);
+      T.s[4] += bil_u(yb, y);                   // u = ybar . y
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
     }
     vertex_row(ev, wb, t);                      // xbar += wbar eps/
-    bilinears(wb, x, s, u);                     // e_i = -wbar g^i x
+    T.e[0] -= bil_s1(wb, x);                    // e_i = -wbar g^i x
+    T.e[1] -= bil_s2(wb, x);
+    T.e[2] -= bil_s3(wb, x);
   } else {
     vertex_row(ev, x, w);                       // w = x eps/
     if (in.post) {
       const Real* P = s_q + in.post * 5;
-      Real y[8];
-      prop_row(P, w, y);                        // y = w P
       prop_col(P, yb, wb);                      // wbar = P ybar
-      bilinears(w, yb, s, u);                   // s_mu = w g^mu ybar
-      Cf<Real> u2, sd[4];
-      bilinears(y, yb, sd, u2);                 // u = y . ybar
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) T.s[mu] += s[mu].re;
-      T.s[4] += u2.re;
+      T.s[0] += bil_s0(w, yb);                  // s_mu = w g^mu ybar
+      T.s[1] += bil_s1(w, yb);
+      T.s[2] += bil_s2(w, yb);
+      T.s[3] += bil_s3(w, yb);
+      T.s[4] += bil_u(y, yb);                   // u = y . ybar
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) wb[i] = yb[i];
     }
     vertex_col(ev, wb, t);                      // xbar += eps/ wbar
-    bilinears(x, wb, s, u);                     // e_i = -x g^i wbar
+    T.e[0] -= bil_s1(x, wb);                    // e_i = -x g^i wbar
+    T.e[1] -= bil_s2(x, wb);
+    T.e[2] -= bil_s3(x, wb);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) xbar[i] += t[i];
-#pragma unroll
-  for (int i = 1; i < 4; ++i) T.e[i - 1] -= s[i].re;
 }
 
 // Reverse of one phase: every instruction passes its outputs' adjoints to its
@@ -179,12 +181,14 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
       if (in.src < 0) load8(s_spin + (in.side * 2 + (in.side == 0 ? p.fixed_sin : p.fixed_sout)) * 8, x);
       else load_cur(s_cur, in.src, 1, 0, x);
       load_cur(s_adj, in.dst, 1, 0, yb);
+      Real y[8];
+      if (in.post) load_cur(s_cur, in.dst, 1, 0, y);
       ParTerms<Real> T;
 #pragma unroll
       for (int c = 0; c < 5; ++c) T.s[c] = (Real)0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) T.e[c] = (Real)0;
-      backprop_terms(in, pol, x, yb, s_q, s_eps, T, xb);
+      backprop_terms(in, pol, x, yb, y, s_q, s_eps, T, xb);
       if (in.post && !(sizeof(Real) == 4 && in.pad)) {
         double* A = s_acc_s + in.post * 5;
 #pragma unroll
@@ -243,8 +247,11 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
           const int hi = (vp >> b) << (b + 1);
 #pragma unroll
           for (int pol = 0; pol < 2; ++pol) {
-            load_cur(s_adj, in.dst, nv, hi | (pol << b) | lo, yb);
-            backprop_terms(in, pol, x, yb, s_q, s_eps, T[pol], xb);
+            const int var = hi | (pol << b) | lo;
+            Real y[8];
+            load_cur(s_adj, in.dst, nv, var, yb);
+            if (in.post) load_cur(s_cur, in.dst, nv, var, y);
+            backprop_terms(in, pol, x, yb, y, s_q, s_eps, T[pol], xb);
           }
           if (in.src >= 0) atomic_add_cur(s_adj + (size_t)(in.src + vp) * 8, 0, xb);
         }
