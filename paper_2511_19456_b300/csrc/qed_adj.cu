@@ -8,7 +8,9 @@
 // xbar = W^T zbar and contributes zbar^T dW x for parameters inside W.
 //
 // Per point:
-//   1. forward pass (as the forward kernel) -> M_l, |M|^2;
+//   1. forward pass -> M_l, |M|^2: the currents as in the forward kernel;
+//      per photon set, M_l += (sum_b R'_b) . (sum_a L_a), the distributive
+//      form of the set's joins (the same leaf sums as in step 3);
 //   2. seeds Mbar_l = conj(M_l) in shared memory;
 //   3. for every photon set S: rebuild the set's currents (sub-currents are
 //      recomputed, not stored), transposed joins give the leaf adjoints
@@ -342,6 +344,26 @@ __device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) 
 
 }  // namespace
 
+// Leaf sums of photon set se, Lsum[v] = sum_a L_a[v] and Rsum[v] = sum_b R'_b[v]
+// for every variant v, into the adjoint slots of leaf 1 of each side (leaf 0
+// when a side has one leaf); returns those slots.  The set's leaf adjoints
+// are written only after the sums are read.
+template <int TEAM, int NL, int NR, int NVL, int NVR, typename Real>
+__device__ __forceinline__ void leaf_sums(const SetEntry& se, int lane, const Real* s_cur, Real* s_adj,
+                                          int& sum_l, int& sum_r) {
+  sum_l = NL > 1 ? se.leaf_l + NVL : se.leaf_l;
+  sum_r = NR > 1 ? se.leaf_r + NVR : se.leaf_r;
+  for (int it = lane; it < (NVL + NVR) * 8; it += TEAM) {
+    const bool left = it < NVL * 8;
+    const int q = left ? it : it - NVL * 8;
+    const int cnt = left ? NL : NR, nv = left ? NVL : NVR;
+    const Real* src = s_cur + (size_t)(left ? se.leaf_l : se.leaf_r) * 8;
+    Real sum = (Real)0;
+    for (int a = 0; a < cnt; ++a) sum += src[(size_t)a * nv * 8 + q];
+    s_adj[(size_t)(left ? sum_l : sum_r) * 8 + q] = sum;
+  }
+}
+
 // Up to 256 threads per block (one team when TEAM > 32); up to 255
 // registers per thread for the spin-summed FP64 form, 128 for the others.
 template <int K, bool SUMMED, typename Real, int TEAM, bool GMEM>
@@ -412,7 +434,34 @@ qed_adj_kernel(const KParams p) {
                                       s_cur);
         team_sync<TEAM>();
       }
-      join_set<K, SUMMED, Real, TEAM, 1>(se, SUMMED ? p.lane_tab + ((size_t)s << N) : nullptr, lane, s_cur, acc);
+      // M_l = sum_{a,b} R'_b . L_a = (sum_b R'_b) . (sum_a L_a): the backward
+      // pass needs only M_l, so the set's leaves are summed first and each
+      // state takes one dot (one compensated step in the mixed form)
+      int sum_l, sum_r;
+      leaf_sums<TEAM, NL, NR, NVL, NVR, Real>(se, lane, s_cur, s_adj, sum_l, sum_r);
+      team_sync<TEAM>();
+      if constexpr (SUMMED) {
+        const unsigned tv = __ldg(p.lane_tab + ((size_t)s << N) + ((unsigned)lane & ALL));
+        const int vl = (int)(tv & 0xffu) << 1, vr = (int)(tv >> 8) << 1;
+#pragma unroll
+        for (int si = 0; si < 2; ++si)
+#pragma unroll
+          for (int so = 0; so < 2; ++so) {
+            Real l[8], r[8];
+            load_cur(s_adj, sum_l, NVL, vl + si, l);
+            load_cur(s_adj, sum_r, NVR, vr + so, r);
+            Real yr = (Real)0, yi = (Real)0;
+            dot_acc(r, l, yr, yi);
+            acc[si * 2 + so].add(yr, yi);
+          }
+      } else if (lane == 0) {
+        Real l[8], r[8];
+        load_cur(s_adj, sum_l, 1, 0, l);
+        load_cur(s_adj, sum_r, 1, 0, r);
+        Real yr = (Real)0, yi = (Real)0;
+        dot_acc(r, l, yr, yi);
+        acc[0].add(yr, yi);
+      }
       team_sync<TEAM>();
     }
 
@@ -466,17 +515,8 @@ qed_adj_kernel(const KParams p) {
       // then one product per leaf variant into the adjoint slots of leaf 0,
       // then a copy to every other leaf.
       {
-        const int sum_l = NL > 1 ? se.leaf_l + NVL : se.leaf_l;
-        const int sum_r = NR > 1 ? se.leaf_r + NVR : se.leaf_r;
-        for (int it = lane; it < (NVL + NVR) * 8; it += TEAM) {
-          const bool left = it < NVL * 8;
-          const int q = left ? it : it - NVL * 8;
-          const int cnt = left ? NL : NR, nv = left ? NVL : NVR;
-          const Real* src = s_cur + (size_t)(left ? se.leaf_l : se.leaf_r) * 8;
-          Real sum = (Real)0;
-          for (int a = 0; a < cnt; ++a) sum += src[(size_t)a * nv * 8 + q];
-          s_adj[(size_t)(left ? sum_l : sum_r) * 8 + q] = sum;
-        }
+        int sum_l, sum_r;
+        leaf_sums<TEAM, NL, NR, NVL, NVR, Real>(se, lane, s_cur, s_adj, sum_l, sum_r);
         team_sync<TEAM>();
         constexpr int NITEM = (NVL + NVR) * 4;
         constexpr int PER = (NITEM + TEAM - 1) / TEAM;
