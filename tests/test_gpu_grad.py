@@ -97,6 +97,23 @@ def test_fixed_state_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
     assert np.all(err <= mixed_tol(k, kap)), (err.max(), int(err.argmax()))
 
 
+@pytest.mark.parametrize("k,summed,npts", [(3, True, 64), (4, True, 32), (5, False, 64), (6, False, 64)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_m2_vs_oracle(orc, k, summed, npts, precision):
+    """|M|^2 from the adjoint (spin-summed: each photon set joined through its
+    leaf sums, one dot per state; one fixed state: per-diagram joins) meets
+    the forward kernels' bounds."""
+    from tests.test_gpu_parity import fp64_tol, mixed_tol
+    mom = ps.points(k, npts, 1.0 + k, seed=640 + k)
+    hel = None if summed else fixed_hel(k)
+    mask = orc.all_summed(k) if summed else 0
+    m2, _ = gpu_grad(Plan(k, summed=summed, hel=hel, precision=precision), mom)
+    ref, kap = orc.m2(mom, sum_mask=mask, hel=hel, kappa=True)
+    rel = np.abs(m2 / ref - 1.0)
+    print(f"\nadjoint |M|^2 k={k} summed={summed} {precision}: max rel {rel.max():.3e}")
+    assert np.all(rel <= (fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)))
+
+
 def test_autograd_function():
     from paper_2511_19456_b300.autograd import m2
     k = 3

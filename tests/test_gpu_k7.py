@@ -30,6 +30,18 @@ def test_k7_summed_vs_stored_oracle(precision):
         assert np.median(rel) <= MIXED_MEDIAN_TOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_k7_adjoint_m2_vs_stored_oracle(precision):
+    """|M|^2 from the adjoint (its forward pass joins each photon set through
+    the leaf sums) against the stored oracle values, with the forward bounds."""
+    mom, ref, kap = load_k7()
+    m2, _ = Plan(7, precision=precision).eval_grad(torch.from_numpy(mom).cuda())
+    rel = np.abs(m2.cpu().numpy() / ref - 1.0)
+    print(f"\nk=7 adjoint |M|^2 {precision}: max rel {rel.max():.3e} median {np.median(rel):.3e}")
+    tol = np.maximum(1e-12, 64 * U64 * kap) if precision == "fp64" else 32 * 15 * U32 * np.maximum(kap, 1)
+    assert np.all(rel <= tol)
+
+
 def test_k7_mixed_adjoint_vs_fp64_differences():
     mom, _, _ = load_k7()
     mom = mom[:4]
