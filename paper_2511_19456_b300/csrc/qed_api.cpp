@@ -182,12 +182,13 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
   if (!P->kc_adj.fn) return QED_OK;
   const int team = P->kc_adj.team;
   const int block = team > 32 ? team : 32;
-  // one fixed state in FP64, k >= 6: one kept level fewer than fits.  The
-  // adjoint holds currents, their adjoints and FP64 accumulators per team,
-  // so few teams are resident; rebuilding one more level per set buys twice
-  // as many (+6 % at k = 6; the mixed form measured 13 % slower this way)
+  // one fixed state, k >= 6: one kept level fewer than fits.  The adjoint
+  // holds currents, their adjoints and FP64 accumulators per team, so few
+  // teams are resident; rebuilding one more level per set buys more of them
+  // (k = 6: +6 % in FP64, +10 % in the mixed form with its per-set FP32
+  // partial sums)
   int start = std::max(h - 1, r - 1);
-  if (!P->summed && !mixed && k >= 6) start -= 1;
+  if (!P->summed && k >= 6) start -= 1;
   for (int lev = start; lev >= 0; --lev) {
     const int ls = std::min(lev, h - 1), rs = std::min(lev, r - 1);
     Schedule sc;
