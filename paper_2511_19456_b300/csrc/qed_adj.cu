@@ -9,9 +9,9 @@
 //
 // Per point:
 //   1. forward pass -> M_l, |M|^2: the currents as in the forward kernel;
-//      spin-summed, per photon set M_l += (sum_b R'_b) . (sum_a L_a), the
-//      distributive form of the set's joins (the same leaf sums as in step
-//      3); one fixed state, the forward kernel's per-diagram joins;
+//      per photon set M_l += (sum_b R'_b) . (sum_a L_a), the distributive
+//      form of the set's joins (the same leaf sums as in step 3); one fixed
+//      state in mixed precision keeps the per-diagram joins;
 //   2. seeds Mbar_l = conj(M_l) in shared memory;
 //   3. for every photon set S: rebuild the set's currents (sub-currents are
 //      recomputed, not stored), transposed joins give the leaf adjoints
@@ -435,31 +435,40 @@ qed_adj_kernel(const KParams p) {
                                       s_cur);
         team_sync<TEAM>();
       }
-      if constexpr (SUMMED) {
+      if constexpr (!SUMMED && sizeof(Real) == 4) {
+        // one fixed state, mixed: the per-diagram joins.  They are few, and
+        // FP32 leaf sums would lose the accuracy of the compensated diagram
+        // sum where the diagrams cancel.
+        join_set<K, false, Real, TEAM, 1>(se, nullptr, lane, s_cur, acc);
+      } else {
         // M_l = sum_{a,b} R'_b . L_a = (sum_b R'_b) . (sum_a L_a): the backward
         // pass needs only M_l, so the set's leaves are summed first and each
-        // state takes one dot (one compensated step in the mixed form).  One
-        // fixed state keeps the per-diagram joins: they are few, and FP32
-        // leaf sums would lose the accuracy of the compensated diagram sum
-        // where the diagrams cancel.
+        // state takes one dot (one compensated step in the mixed form)
         int sum_l, sum_r;
         leaf_sums<TEAM, NL, NR, NVL, NVR, Real>(se, lane, s_cur, s_adj, sum_l, sum_r);
         team_sync<TEAM>();
-        const unsigned tv = __ldg(p.lane_tab + ((size_t)s << N) + ((unsigned)lane & ALL));
-        const int vl = (int)(tv & 0xffu) << 1, vr = (int)(tv >> 8) << 1;
+        if constexpr (SUMMED) {
+          const unsigned tv = __ldg(p.lane_tab + ((size_t)s << N) + ((unsigned)lane & ALL));
+          const int vl = (int)(tv & 0xffu) << 1, vr = (int)(tv >> 8) << 1;
 #pragma unroll
-        for (int si = 0; si < 2; ++si)
+          for (int si = 0; si < 2; ++si)
 #pragma unroll
-          for (int so = 0; so < 2; ++so) {
-            Real l[8], r[8];
-            load_cur(s_adj, sum_l, NVL, vl + si, l);
-            load_cur(s_adj, sum_r, NVR, vr + so, r);
-            Real yr = (Real)0, yi = (Real)0;
-            dot_acc(r, l, yr, yi);
-            acc[si * 2 + so].add(yr, yi);
-          }
-      } else {
-        join_set<K, false, Real, TEAM, 1>(se, nullptr, lane, s_cur, acc);
+            for (int so = 0; so < 2; ++so) {
+              Real l[8], r[8];
+              load_cur(s_adj, sum_l, NVL, vl + si, l);
+              load_cur(s_adj, sum_r, NVR, vr + so, r);
+              Real yr = (Real)0, yi = (Real)0;
+              dot_acc(r, l, yr, yi);
+              acc[si * 2 + so].add(yr, yi);
+            }
+        } else if (lane == 0) {
+          Real l[8], r[8];
+          load_cur(s_adj, sum_l, 1, 0, l);
+          load_cur(s_adj, sum_r, 1, 0, r);
+          Real yr = (Real)0, yi = (Real)0;
+          dot_acc(r, l, yr, yi);
+          acc[0].add(yr, yi);
+        }
       }
       team_sync<TEAM>();
     }
