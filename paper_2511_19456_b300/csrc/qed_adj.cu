@@ -30,11 +30,11 @@
 //        finally dE_j/dk_j = k_j / |k_j|.
 // Q, D and eps are real, so only the real parts of s_mu, u and e_i are
 // accumulated.  The accumulators are FP64 in shared memory (atomic adds);
-// currents and their adjoints are in the working precision.  One fixed state in mixed
-// precision: the terms of one photon set are first summed in FP32 (one slot
-// per propagator of the set, one per photon), then added to the FP64
-// accumulators once per set; FP64 atomics on words that every lane of the
-// team hits took most of that adjoint's time.
+// currents and their adjoints are in the working precision.  One fixed
+// state in mixed precision: the terms of one photon set are first summed in
+// FP32 (one slot per propagator of the set, one per photon), then added to
+// the FP64 accumulators once per set, so that the lanes of a team do not
+// all contend for the same FP64 words.
 #include <cuda_runtime.h>
 
 #include "qed_team.cuh"
