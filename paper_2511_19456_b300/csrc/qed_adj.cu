@@ -366,10 +366,14 @@ __device__ __forceinline__ void leaf_sums(const SetEntry& se, int lane, const Re
 }
 
 // Up to 256 threads per block (one team when TEAM > 32); up to 255
-// registers per thread for the spin-summed FP64 form, 128 for the others.
+// registers per thread for the FP64 forms that are spin-summed or have
+// k >= 6 (shared memory holds those to a few warps per SM anyway), 128 for
+// the others.
 template <int K, bool SUMMED, typename Real, int TEAM, bool GMEM>
 __global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256,
-                                  (SUMMED && sizeof(Real) == 8) ? 1 : 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
+                                  (sizeof(Real) == 8 && (SUMMED || K >= 6))
+                                      ? 1
+                                      : 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
 qed_adj_kernel(const KParams p) {
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;
@@ -600,6 +604,7 @@ qed_adj_kernel(const KParams p) {
     }
 
     // ---- 5. parameters -> outgoing photon momenta (FP64)
+#pragma unroll 1
     for (int mask = lane; mask < NSUB; mask += TEAM) {
       if (mask == 0 || mask == (int)ALL) continue;
       double q0 = s_mom[0], q1 = s_mom[1], q2 = s_mom[2], q3 = s_mom[3];
@@ -614,19 +619,33 @@ qed_adj_kernel(const KParams p) {
       D = __dsub_rn(D, __dmul_rn(q2, q2));
       D = __dsub_rn(D, __dmul_rn(q3, q3));
       D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
-      const double* Ac = s_acc_s + mask * 5;
+      // df/dQ_T^mu, in place of the subset's accumulator
+      double* Ac = s_acc_s + mask * 5;
       const double Q[4] = {q0, q1, q2, q3};
+      const double two_inv_d = 2.0 / D;
       double qb[4];
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
         const double eta = mu == 0 ? 1.0 : -1.0;
-        qb[mu] = 2.0 * eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) / D;
+        qb[mu] = eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) * two_inv_d;
       }
-      for (int j = 1; j < N; ++j)
-        if (mask & (1 << j))
 #pragma unroll
-          for (int mu = 0; mu < 4; ++mu) atomicAdd(s_kbar + 4 * j + mu, -qb[mu]);
+      for (int mu = 0; mu < 4; ++mu) Ac[mu] = qb[mu];
     }
+    team_sync<TEAM>();
+    // Q_T = p + k_0 - sum_{j in T, j >= 1} k_j: d f/d k_j^mu = -sum_{T containing j}
+    // df/dQ_T^mu, one lane per (j, mu) over the 2^(n-1) subsets that contain j
+    // (plain stores: no two lanes share a word)
+    for (int it = lane; it < K * 4; it += TEAM) {
+      const int j = 1 + (it >> 2), mu = it & 3;
+      const int lo = (1 << j) - 1;
+      double a = 0.0;
+#pragma unroll 1
+      for (int r = 0; r < (1 << (N - 1)) - 1; ++r)   // r = 2^(n-1) - 1 would be the full set
+        a += s_acc_s[(((r >> j) << (j + 1)) | (1 << j) | (r & lo)) * 5 + mu];
+      s_kbar[4 * j + mu] = -a;
+    }
+    team_sync<TEAM>();
     for (int it = lane; it < 2 * N; it += TEAM) {
       const int j = it >> 1, pb = it & 1;
       if (j == 0) continue;
