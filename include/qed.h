@@ -217,7 +217,11 @@ qed_status qed_eval(qed_plan_t plan, const double* d_momenta, long long n,
  * through the same reduced DAG, sub-currents recomputed per photon set;
  * where a team's currents and adjoints do not fit in shared memory
  * (spin-summed k = 7 in FP64), the plan holds a global scratch for them,
- * allocated at creation.  QED_EUNSUPPORTED for rewrite, ABC and tape plans. */
+ * allocated at creation.  d_out_m2 comes from the adjoint's own forward
+ * pass.  It joins each photon set through its leaf sums,
+ * (sum_b R'_b).(sum_a L_a), except for one fixed state in mixed precision,
+ * which keeps the per-diagram joins.  It equals qed_eval's result up to
+ * rounding.  QED_EUNSUPPORTED for rewrite, ABC and tape plans. */
 qed_status qed_eval_grad(qed_plan_t plan, const double* d_momenta, long long n,
                          double* d_out_m2, double* d_grad, void* stream);
 
