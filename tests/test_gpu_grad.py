@@ -114,6 +114,30 @@ def test_adjoint_m2_vs_oracle(orc, k, summed, npts, precision):
     assert np.all(rel <= (fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_k7_fixed_state_adjoint_vs_oracle_gradient(orc, precision):
+    """k = 7 (40,320 diagrams), one fixed state: the FP64 form allows 255
+    registers per thread and the mixed form keeps one level fewer, with
+    several partial-sum slots per photon set."""
+    from tests.test_gpu_parity import fp64_tol, mixed_tol
+    k = 7
+    mom = ps.points(k, 32, 8.0, seed=650)
+    hel = fixed_hel(k)
+    m2, g = gpu_grad(Plan(k, summed=False, hel=hel, precision=precision), mom)
+    ref_m2, ref_g = orc.grad(mom, sum_mask=0, hel=hel)
+    _, kap = orc.m2(mom, sum_mask=0, hel=hel, kappa=True)
+    err = np.abs(g - ref_g).max(axis=(1, 2)) / np.abs(ref_g).max(axis=(1, 2))
+    rel = np.abs(m2 / ref_m2 - 1.0)
+    print(f"\nk=7 fixed {precision} adjoint: grad max rel err {err.max():.3e}, |M|^2 max rel {rel.max():.3e} "
+          f"(kappa max {kap.max():.1f})")
+    if precision == "fp64":
+        assert np.all(err <= np.maximum(1e-10, 64 * U64 * kap))
+        assert np.all(rel <= fp64_tol(kap))
+    else:
+        assert np.all(err <= mixed_tol(k, kap))
+        assert np.all(rel <= mixed_tol(k, kap))
+
+
 def test_autograd_function():
     from paper_2511_19456_b300.autograd import m2
     k = 3
