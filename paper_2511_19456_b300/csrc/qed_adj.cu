@@ -30,10 +30,10 @@
 //        finally dE_j/dk_j = k_j / |k_j|.
 // Q, D and eps are real, so only the real parts of s_mu, u and e_i are
 // accumulated.  The accumulators are FP64 in shared memory (atomic adds);
-// currents and their adjoints are in the working precision.  One fixed
-// state in mixed precision: the terms of one photon set are first summed in
-// FP32 (one slot per propagator of the set, one per photon), then added to
-// the FP64 accumulators once per set, so that the lanes of a team do not
+// currents and their adjoints are in the working precision.  In mixed
+// precision the terms of one photon set are first summed in FP32 (one slot
+// per propagator of the set, one per photon and polarisation), then added
+// to the FP64 accumulators once per set, so that the lanes of a team do not
 // all contend for the same FP64 words.
 #include <cuda_runtime.h>
 
@@ -270,16 +270,38 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
             for (int c = 0; c < 3; ++c) T[q].e[c] += __shfl_xor_sync(0xffffffffu, T[q].e[c], off);
         }
         if (valid && (vp & (G - 1)) == 0) {
-          if (in.post) {
-            double* A = s_acc_s + in.post * 5;
+          if constexpr (sizeof(Real) == 4) {
+            // mixed: FP32 partial sums of the photon set (flush_partials);
+            // the kept levels' propagator terms go to FP64 directly
+            if (in.post) {
+              if (in.pad) {
+                float* A = s_part + (in.pad - 1) * 5;
 #pragma unroll
-            for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T[0].s[c]);
-          }
+                for (int c = 0; c < 5; ++c) atomicAdd(A + c, T[0].s[c]);
+              } else {
+                double* A = s_acc_s + in.post * 5;
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            double* E = s_acc_e + (in.photon * 2 + q) * 3;
+                for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T[0].s[c]);
+              }
+            }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T[q].e[c]);
+            for (int q = 0; q < 2; ++q) {
+              float* E = s_part + p.n_part * 5 + (in.photon * 2 + q) * 3;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) atomicAdd(E + c, T[q].e[c]);
+            }
+          } else {
+            if (in.post) {
+              double* A = s_acc_s + in.post * 5;
+#pragma unroll
+              for (int c = 0; c < 5; ++c) atomicAdd(A + c, (double)T[0].s[c]);
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              double* E = s_acc_e + (in.photon * 2 + q) * 3;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) atomicAdd(E + c, (double)T[q].e[c]);
+            }
           }
         }
       }
@@ -287,11 +309,12 @@ __device__ __forceinline__ void backprop_phase(const Phase& ph, int lane, const 
   }
 }
 
-// Fixed-state mixed adjoint: adds the FP32 partial sums to the FP64
-// accumulators and clears them; set >= 0 flushes that set's propagator
-// slots and the photon terms, set < 0 the photon terms only.  Every slot of
-// a set names a different propagator, so no two lanes add to the same word.
-template <int TEAM, int N>
+// Mixed adjoint: adds the FP32 partial sums to the FP64 accumulators and
+// clears them; set >= 0 flushes that set's propagator slots and the photon
+// terms, set < 0 the photon terms only.  Every slot of a set names a
+// different propagator, so no two lanes add to the same word.  One fixed
+// state keeps one polarisation per photon, the spin-summed form both.
+template <int TEAM, int N, bool SUMMED>
 __device__ __forceinline__ void flush_partials(const KParams& p, int set, int lane, float* s_part,
                                                double* s_acc_s, double* s_acc_e) {
   if (set >= 0) {
@@ -304,11 +327,18 @@ __device__ __forceinline__ void flush_partials(const KParams& p, int set, int la
     }
   }
   float* e = s_part + p.n_part * 5;
-  for (int i = lane; i < N * 3; i += TEAM) {
-    const int j = i / 3;
-    const int pol = (int)((p.fixed_pol_bits >> j) & 1u);
-    s_acc_e[(j * 2 + pol) * 3 + i % 3] += (double)e[i];
-    e[i] = 0.f;
+  if constexpr (SUMMED) {
+    for (int i = lane; i < N * 6; i += TEAM) {
+      s_acc_e[i] += (double)e[i];
+      e[i] = 0.f;
+    }
+  } else {
+    for (int i = lane; i < N * 3; i += TEAM) {
+      const int j = i / 3;
+      const int pol = (int)((p.fixed_pol_bits >> j) & 1u);
+      s_acc_e[(j * 2 + pol) * 3 + i % 3] += (double)e[i];
+      e[i] = 0.f;
+    }
   }
 }
 
@@ -391,7 +421,7 @@ qed_adj_kernel(const KParams p) {
   // not fit, in a global scratch slot of the team; the rest stays in shared
   // memory.  A separate instance, so that the shared-memory one addresses
   // its currents as shared memory.
-  constexpr bool PART = !SUMMED && sizeof(Real) == 4;   // FP32 partial sums per photon set
+  constexpr bool PART = sizeof(Real) == 4;   // FP32 partial sums per photon set
   const AdjLayout A = adj_layout(K, (int)sizeof(Real), GMEM ? 0 : p.ncur, SUMMED, PART ? p.n_part : 0);
   const TeamLayout& L = A.fwd;
   const int lane = threadIdx.x & (TEAM - 1);
@@ -506,7 +536,7 @@ qed_adj_kernel(const KParams p) {
       for (int i = lane; i < N * 6; i += TEAM) s_acc_e[i] = 0.0;
       for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
       if constexpr (PART)
-        for (int i = lane; i < p.n_part * 5 + N * 3; i += TEAM) s_part[i] = 0.f;
+        for (int i = lane; i < p.n_part * 5 + N * (SUMMED ? 6 : 3); i += TEAM) s_part[i] = 0.f;
     }
     team_sync<TEAM>();
 
@@ -587,7 +617,7 @@ qed_adj_kernel(const KParams p) {
         team_sync<TEAM>();
       }
       if constexpr (PART) {
-        flush_partials<TEAM, N>(p, s, lane, s_part, s_acc_s, s_acc_e);
+        flush_partials<TEAM, N, SUMMED>(p, s, lane, s_part, s_acc_s, s_acc_e);
         team_sync<TEAM>();
       }
     }
@@ -599,7 +629,7 @@ qed_adj_kernel(const KParams p) {
       team_sync<TEAM>();
     }
     if constexpr (PART) {
-      flush_partials<TEAM, N>(p, -1, lane, s_part, s_acc_s, s_acc_e);
+      flush_partials<TEAM, N, SUMMED>(p, -1, lane, s_part, s_acc_s, s_acc_e);
       team_sync<TEAM>();
     }
 

@@ -146,7 +146,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
 // The adjoint keeps the forward currents and their adjoints in shared
 // memory: take the deepest kept levels (ls, rs) whose team fits; if none
 // fits, qed_eval_grad reports QED_EUNSUPPORTED for this plan.
-// Fixed-state mixed adjoint: every photon set gets one FP32 partial-sum slot
+// Mixed adjoint: every photon set gets one FP32 partial-sum slot
 // per distinct propagator of its instructions.  Sets the slot (plus one) into
 // the instructions' pad field, fills tab[set][slot] with the propagator's
 // photon set and returns the slots per set.  The kept levels' instructions
@@ -201,7 +201,7 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
     }
     const int ncur = sc.stored_currents + sc.local_currents;
     std::vector<uint16_t> part_tab;
-    const int n_part = (!P->summed && mixed) ? assign_partial_slots(sc, &part_tab) : 0;
+    const int n_part = mixed ? assign_partial_slots(sc, &part_tab) : 0;
     AdjLayout A = adj_layout(k, mixed ? 4 : 8, ncur, P->summed, n_part);
     const size_t smem = (size_t)(block / team) * A.bytes;
     if (smem > (size_t)dev_smem) continue;

@@ -66,7 +66,7 @@ struct qed_plan_s {
   SumInstr* d_sinstr = nullptr;
   uint16_t* d_lane_tab = nullptr;   // spin-summed plans: leaf variants per (set, lane)
   uint16_t* d_dep_tab = nullptr;    // spin-summed plans: polarisation patterns per (set, leaf variant)
-  uint16_t* d_part_tab = nullptr;   // fixed-state mixed adjoint: propagator of each partial-sum slot per set
+  uint16_t* d_part_tab = nullptr;   // mixed adjoint: propagator of each partial-sum slot per set
   int n_part = 0;
   int device = 0;
   // staging for qed_eval_host (one call at a time per plan: stage_lock)

@@ -92,9 +92,10 @@ struct AdjLayout {
 
 // Parameter accumulators: the real parts of 5 propagator terms per photon
 // subset and of 3 polarisation terms per photon and polarisation.
-// n_part > 0 (one fixed state, mixed): FP32 partial sums of one photon set's
+// n_part > 0 (mixed precision): FP32 partial sums of one photon set's
 // parameter terms, n_part propagator slots of 5 reals and 3 reals per
-// photon, added to the FP64 accumulators once per set.
+// photon (6 when the spin is summed: both polarisations), added to the FP64
+// accumulators once per set.
 QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_part = 0) {
   const int n = k + 1;
   AdjLayout A;
@@ -105,7 +106,7 @@ QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_p
   A.acc_s = off; off = align16(off + (1 << n) * 5 * 8);
   A.acc_e = off; off = align16(off + n * 2 * 3 * 8);
   A.kbar = off;  off = align16(off + n * 4 * 8);
-  A.part = off;  off = align16(off + (n_part > 0 ? (n_part * 5 + n * 3) * 4 : 0));
+  A.part = off;  off = align16(off + (n_part > 0 ? (n_part * 5 + n * (summed ? 6 : 3)) * 4 : 0));
   A.bytes = off;
   return A;
 }
@@ -141,7 +142,7 @@ struct KParams {
   // scratch of adj_scratch_team bytes per team (currents, then adjoints)
   void* adj_scratch;
   long long adj_scratch_team;
-  // fixed-state mixed adjoint: for set s, entry [s][i] is the propagator
+  // mixed adjoint: for set s, entry [s][i] is the propagator
   // photon set of partial-sum slot i (0: unused); an instruction of the set
   // names its slot as pad - 1 (pad = 0: no slot, direct FP64 accumulation)
   const uint16_t* part_tab;

@@ -114,6 +114,28 @@ def test_adjoint_m2_vs_oracle(orc, k, summed, npts, precision):
     assert np.all(rel <= (fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)))
 
 
+@pytest.mark.parametrize("k,npts", [(1, 64), (2, 64), (3, 32), (4, 16), (5, 4)])
+def test_summed_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
+    """All spin states, mixed precision (FP32 parameter terms summed per
+    photon set before the FP64 accumulators): the forward mixed bound.  The
+    error is taken relative to the gradient's natural scale per point,
+    max(max|g_ref|, |M|^2 / min_j |k_j|): where |M|^2 is near stationary in
+    some k_j, the FP32 rounding of its terms stays of order u32 |M|^2 / |k|
+    while the gradient itself vanishes."""
+    from tests.test_gpu_parity import mixed_tol
+    mom = ps.points(k, npts, 1.0 + k, seed=660 + k)
+    _, g = gpu_grad(Plan(k, precision="mixed"), mom)
+    ref_m2, ref_g = orc.grad(mom, sum_mask=orc.all_summed(k))
+    _, kap = orc.m2(mom, sum_mask=orc.all_summed(k), kappa=True)
+    kmin = np.linalg.norm(mom[:, 3:, 1:], axis=2).min(axis=1)
+    gmax = np.abs(ref_g).max(axis=(1, 2))
+    err = np.abs(g - ref_g).max(axis=(1, 2)) / np.maximum(gmax, ref_m2 / kmin)
+    w = int(err.argmax())
+    print(f"\nsummed mixed adjoint k={k}: grad max rel err {err.max():.3e} median {np.median(err):.3e} "
+          f"(worst point: max|g| {gmax[w]:.3e}, |M|^2/|k|min {ref_m2[w] / kmin[w]:.3e})")
+    assert np.all(err <= mixed_tol(k, kap)), (err.max(), w)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_k7_fixed_state_adjoint_vs_oracle_gradient(orc, precision):
     """k = 7 (40,320 diagrams), one fixed state: the FP64 form allows 255
