@@ -56,9 +56,10 @@ qed_fwd_fixed64_kernel(const KParams p) {
 }
 
 // One fixed state, mixed: 128-thread blocks of up to 128 registers per
-// thread, so that the unrolled rounds of the join do not spill.
+// thread, so that the unrolled rounds of the join do not spill; at k = 6,
+// 102 registers (5 blocks per SM), which it fits without spilling.
 template <int K, int TEAM>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, K == 6 ? 5 : 4)
 qed_fwd_fixed_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tpc = blockDim.x / TEAM;
