@@ -32,8 +32,10 @@
  * arguments are validated before any launch; N = 0 returns QED_OK without a
  * launch.  Non-finite momenta give non-finite outputs and are not errors.
  * qed_eval and qed_eval_grad allocate nothing and do not synchronise the
- * host; a plan is immutable after creation and may be used from several
- * streams at once.
+ * host.  A plan's tables are immutable after creation, and evaluations of
+ * one plan may be issued from several host threads and streams at once;
+ * the one exception, the plan-owned gradient scratch of spin-summed k = 7 in
+ * FP64, is described at qed_eval_grad.
  */
 #ifndef QED_H
 #define QED_H
@@ -97,7 +99,26 @@ typedef struct {
   int smem_bytes_per_team;
   int precision;               /* qed_precision                            */
   int reduction_steps;         /* tape plans: node reductions applied      */
+  int kernel_form;             /* forward kernel in use: qed_kernel_form   */
+  int kernel_forms;            /* forms this plan has: bit f set for form f */
+  int block_threads;           /* launch shape of that kernel: threads per */
+  int grid_blocks;             /* block, and blocks of the persistent grid */
 } qed_plan_info_t;
+
+/* Forward kernel forms of a plan.  The DAG builder either linearises the
+ * DAG into instruction tables or emits a straight-line specialised kernel
+ * at build time (the paper's framework generates straight-line code from
+ * the scheduled DAG, Sec. II-A; Sec. III-E measures full inlining).
+ *   QED_KERNEL_TABLE: one kernel per (k, spin mode, precision) that reads the
+ *     plan's linear schedule (instruction, phase and photon-set tables) from
+ *     device memory at run time.  Every plan has it.
+ *   QED_KERNEL_SPECIALISED: a kernel generated from the same schedule when
+ *     the library is built (csrc/qed_codegen.cpp), with every instruction
+ *     expanded into straight-line code whose photon, polarisation, source,
+ *     destination and propagator are literals.  Spin-summed plans of the
+ *     node-reduced DAG with k <= 4.
+ * Both compute the same DAG; their results agree to rounding. */
+typedef enum { QED_KERNEL_TABLE = 0, QED_KERNEL_SPECIALISED = 1 } qed_kernel_form;
 
 /* Counts of the CDAG of one spin state, computed on the host without a GPU
  * (paper Table I and Fig. graph_size).  For k <= 7 the DAG is built node by
@@ -205,6 +226,28 @@ qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* 
 
 qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 
+/* Selects the forward kernel form (qed_kernel_form) that qed_eval,
+ * qed_eval_host and qed_cross_section launch.  A new plan starts with the
+ * specialised form where it has one.  The switch is atomic: an evaluation
+ * running on another stream uses one form or the other.
+ * Errors: QED_EINVAL (NULL plan, unknown form), QED_EUNSUPPORTED (the plan
+ * has no such form).  The paper has no counterpart: its framework emits
+ * only generated code. */
+qed_status qed_plan_set_kernel_form(qed_plan_t plan, int form);
+
+/* Autotuner of a plan's forward launch: kernel form and block size picked
+ * by measurement.  Times every form the plan has
+ * with blocks of 32, 64, 128 and 256 threads (those that hold whole teams,
+ * that the kernel's launch bounds and the shared memory allow) on the
+ * caller's device buffers d_momenta[n][k+3][4] -> d_out_m2[n] (n > 0; the
+ * outputs are overwritten), with CUDA events on `stream`, and keeps the
+ * fastest.  Returns it in *form, *block and *best_ms (each may be NULL).
+ * Synchronous; the plan must not be evaluated from another thread while it
+ * is tuned.  Errors: QED_EINVAL (NULL or misaligned buffers, n <= 0),
+ * QED_ECUDA.  Not in the paper. */
+qed_status qed_plan_tune(qed_plan_t plan, const double* d_momenta, long long n, double* d_out_m2, void* stream,
+                         int* form, int* block, double* best_ms);
+
 /* out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4
  * doubles, 8-byte aligned; d_out_m2: device pointer to N doubles; stream: a
  * cudaStream_t (NULL = legacy default stream).  Asynchronous. */
@@ -221,9 +264,33 @@ qed_status qed_eval(qed_plan_t plan, const double* d_momenta, long long n,
  * pass.  It joins each photon set through its leaf sums,
  * (sum_b R'_b).(sum_a L_a), except for one fixed state in mixed precision,
  * which keeps the per-diagram joins.  It equals qed_eval's result up to
- * rounding.  QED_EUNSUPPORTED for rewrite, ABC and tape plans. */
+ * rounding.  QED_EUNSUPPORTED for rewrite, ABC and tape plans.
+ *
+ * Plans whose adjoint uses the global scratch (qed_grad_workspace_bytes
+ * reports more than 0): the launches of qed_eval_grad on such a plan run one
+ * after another on the device whatever their streams, each waiting for the
+ * previous one (an event the plan records; no host synchronisation).  Inside
+ * a stream capture no such wait is added, and a graph so captured must not
+ * run at the same time as another use of the plan's scratch.  For
+ * concurrent gradients on one plan, give each caller its own workspace
+ * through qed_eval_grad_ws. */
 qed_status qed_eval_grad(qed_plan_t plan, const double* d_momenta, long long n,
                          double* d_out_m2, double* d_grad, void* stream);
+
+/* Bytes of device workspace that qed_eval_grad_ws needs for this plan's
+ * adjoint: the currents and adjoints of every resident team when they do
+ * not fit in shared memory (spin-summed k = 7 in FP64), else 0.
+ * QED_EUNSUPPORTED for plans without an adjoint.  Not in the paper. */
+qed_status qed_grad_workspace_bytes(qed_plan_t plan, long long* bytes);
+
+/* As qed_eval_grad with the scratch in a caller-owned device buffer
+ * d_workspace of workspace_bytes bytes (256-byte aligned; at least
+ * qed_grad_workspace_bytes, and ignored, may be NULL, when that is 0).
+ * Calls with different workspaces may run concurrently on any streams;
+ * calls that share one race.  QED_EINVAL for a missing, short or misaligned
+ * workspace.  Not in the paper. */
+qed_status qed_eval_grad_ws(qed_plan_t plan, const double* d_momenta, long long n, double* d_out_m2,
+                            double* d_grad, void* d_workspace, long long workspace_bytes, void* stream);
 
 /* End-to-end form of qed_eval on HOST buffers: copies the momenta to the
  * device, evaluates and copies |M|^2 back, chunked so that copies overlap

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libqedm2.so")
 
 QED_OK, QED_EINVAL, QED_ENOMEM, QED_ECUDA, QED_EUNSUPPORTED, QED_EDEVICE_TIMEOUT = range(6)
 QED_FP64, QED_MIXED = 0, 1
+QED_KERNEL_TABLE, QED_KERNEL_SPECIALISED = 0, 1
 
 
 class QedError(RuntimeError):
@@ -50,7 +51,9 @@ class PlanInfo(ctypes.Structure):
                 ("flops_executed_per_point", ctypes.c_longlong),
                 ("flops_literal_s2_per_point", ctypes.c_longlong),
                 ("team_threads", ctypes.c_int), ("smem_bytes_per_team", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reduction_steps", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("reduction_steps", ctypes.c_int),
+                ("kernel_form", ctypes.c_int), ("kernel_forms", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("grid_blocks", ctypes.c_int)]
 
 
 class DagCounts(ctypes.Structure):
@@ -79,6 +82,9 @@ SIGNATURES = [
     ("qed_abc_plan_create", ctypes.c_int, [ctypes.POINTER(AbcProcess), ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(_vp)]),
     ("qed_plan_info", ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    ("qed_plan_set_kernel_form", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("qed_plan_tune", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     ("qed_debug_inject_alloc_failure", ctypes.c_int, [ctypes.c_int]),
     ("qed_reduction_steps", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("qed_tape_export", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(TapeDesc), _vp,
@@ -87,6 +93,8 @@ SIGNATURES = [
                                             ctypes.POINTER(_vp)]),
     ("qed_eval", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),
     ("qed_eval_grad", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, _vp]),
+    ("qed_grad_workspace_bytes", ctypes.c_int, [_vp, ctypes.POINTER(_ll)]),
+    ("qed_eval_grad_ws", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp, _vp, _ll, _vp]),
     ("qed_eval_host", ctypes.c_int, [_vp, _vp, _ll, _vp, _vp]),
     ("qed_plan_destroy", None, [_vp]),
     ("qed_dag_counts", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(DagCounts)]),

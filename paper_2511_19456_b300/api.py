@@ -67,6 +67,38 @@ class Plan:
         check(_lib.lib().qed_plan_info(self._h, ctypes.byref(inf)), "qed_plan_info")
         return {f: getattr(inf, f) for f, _ in _lib.PlanInfo._fields_}
 
+    KERNEL_FORMS = {"table": _lib.QED_KERNEL_TABLE, "specialised": _lib.QED_KERNEL_SPECIALISED}
+
+    @property
+    def kernel_form(self) -> str:
+        """The forward kernel in use: "table" (schedule read from device
+        tables) or "specialised" (straight-line code generated at build time)."""
+        f = self.info()["kernel_form"]
+        return next(name for name, v in self.KERNEL_FORMS.items() if v == f)
+
+    def kernel_forms(self) -> list:
+        """The forms this plan has."""
+        bits = self.info()["kernel_forms"]
+        return [name for name, v in self.KERNEL_FORMS.items() if bits & (1 << v)]
+
+    def set_kernel_form(self, form: str) -> None:
+        check(_lib.lib().qed_plan_set_kernel_form(self._h, self.KERNEL_FORMS[form]), "qed_plan_set_kernel_form")
+
+    def tune(self, momenta, out=None, stream=None) -> dict:
+        """Times every kernel form and block size on these device buffers,
+        keeps the fastest; returns {"form", "block", "ms"}.  Synchronous."""
+        torch = _torch()
+        self._check_momenta(momenta, device=True)
+        n = momenta.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=momenta.device)
+        f, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(_lib.lib().qed_plan_tune(self._h, ctypes.c_void_p(momenta.data_ptr()), n,
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream),
+                                       ctypes.byref(f), ctypes.byref(b), ctypes.byref(ms)), "qed_plan_tune")
+        name = next(nm for nm, v in self.KERNEL_FORMS.items() if v == f.value)
+        return {"form": name, "block": b.value, "ms": ms.value}
+
     def _check_momenta(self, momenta, device: bool):
         torch = _torch()
         if momenta.dtype != torch.float64:
@@ -106,6 +138,30 @@ class Plan:
                                        ctypes.c_void_p(out.data_ptr()),
                                        ctypes.c_void_p(grad.data_ptr()), _stream_handle(stream)),
               "qed_eval_grad")
+        return out, grad
+
+    def grad_workspace_bytes(self) -> int:
+        """Device workspace that eval_grad(workspace=...) needs (0: none)."""
+        v = ctypes.c_longlong()
+        check(_lib.lib().qed_grad_workspace_bytes(self._h, ctypes.byref(v)), "qed_grad_workspace_bytes")
+        return v.value
+
+    def eval_grad_ws(self, momenta, workspace, out=None, grad=None, stream=None):
+        """eval_grad with the adjoint's scratch in a caller-owned device
+        buffer (a uint8 CUDA tensor of at least grad_workspace_bytes())."""
+        torch = _torch()
+        self._check_momenta(momenta, device=True)
+        n = momenta.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=momenta.device)
+        if grad is None:
+            grad = torch.empty((n, self.k, 3), dtype=torch.float64, device=momenta.device)
+        ws_ptr = workspace.data_ptr() if workspace is not None else 0
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        check(_lib.lib().qed_eval_grad_ws(self._h, ctypes.c_void_p(momenta.data_ptr()), n,
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                          ctypes.c_void_p(ws_ptr), ws_bytes, _stream_handle(stream)),
+              "qed_eval_grad_ws")
         return out, grad
 
     def eval_host(self, momenta, out=None, stream=None):

@@ -54,6 +54,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_dep_tab);
   cudaFree(p->d_part_tab);
   cudaFree(p->d_stage);
+  if (p->ev_scratch) cudaEventDestroy(p->ev_scratch);
   for (int i = 0; i < 2; ++i) {
     if (p->ev_h2d[i]) cudaEventDestroy(p->ev_h2d[i]);
     if (p->ev_k[i]) cudaEventDestroy(p->ev_k[i]);
@@ -258,8 +259,10 @@ qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
     if (e == cudaSuccess) e = upload(&P->d_phases_adj, sc.phases);
     if (e == cudaSuccess) e = upload(&P->d_sets_adj, sc.sets);
     if (e == cudaSuccess) e = device_alloc(&P->d_adj_scratch, (size_t)(teams * team_bytes));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_scratch, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e);
     P->adj_scratch_team = team_bytes;
+    P->adj_scratch_bytes = teams * team_bytes;
     P->kc_adj = kg;
     P->sc_adj = std::move(sc);
     P->block_adj = block;
@@ -274,11 +277,28 @@ qed_status launch_eval(const qed_plan_s* P, const double* d_mom, long long n, do
                        cudaStream_t st) {
   if (n == 0) return QED_OK;
   KParams kp = make_params(P, d_mom, n, d_out);
-  const int tpc = P->block / P->kc.team;
+  const qed_plan_s::Form& f = P->forms[P->form.load(std::memory_order_relaxed)];
+  const int tpc = f.block / f.kc.team;
   long long need = (n + tpc - 1) / tpc;
-  int grid = (int)std::min<long long>(need, P->grid);
-  return cuda_status(launch_forward(P->kc.fn, grid, P->block, P->smem, st, kp));
+  int grid = (int)std::min<long long>(need, f.grid);
+  return cuda_status(launch_forward(f.kc.fn, grid, f.block, f.smem, st, kp));
 }
+
+// Shared-memory attribute and resident blocks of one forward form.
+cudaError_t configure_form(qed_plan_s::Form* f, int sms) {
+  cudaError_t e = cudaFuncSetAttribute((const void*)f->kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f->smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)f->kc.fn, f->block, f->smem);
+  f->ok = e == cudaSuccess && per_sm >= 1;
+  f->grid = per_sm * sms;
+  return e;
+}
+
+// The form a new plan starts with, from measurements on B300: the
+// straight-line specialised kernel wherever it exists.
+int default_form(const qed_plan_s* P) { return P->forms[1].ok ? 1 : 0; }
 
 }  // namespace
 
@@ -459,6 +479,26 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
                                                       P->smem);
   if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
   P->grid = per_sm * sms;
+  P->forms[0] = qed_plan_s::Form{P->kc, P->block, P->grid, P->smem, true, L.bytes};
+  if (!rewrite && P->summed) {
+    const SpecKernel sk = spec_forward_kernel(k, mixed);
+    const int spec_ncur = P->sc.stored_currents + P->sc.local_currents;
+    if (sk.fn && sk.team == P->kc.team && sk.ncur == spec_ncur &&
+        sk.team_bytes == team_layout(k, mixed ? 4 : 8, spec_ncur).bytes) {
+      qed_plan_s::Form f{KernelChoice{sk.fn, sk.team}, P->block, 0, 0, false, sk.team_bytes};
+      f.smem = (size_t)(f.block / sk.team) * sk.team_bytes;
+      while (f.smem > (size_t)dev_smem && f.block > sk.team) {
+        f.block /= 2;
+        f.smem = (size_t)(f.block / sk.team) * sk.team_bytes;
+      }
+      if (f.smem <= (size_t)dev_smem) {
+        e = configure_form(&f, sms);
+        if (e != cudaSuccess) { free_plan(P); return cuda_status(e); }
+        P->forms[1] = f;
+      }
+    }
+  }
+  P->form.store(default_form(P));
   if (!rewrite) {
     qed_status as = setup_adjoint(P, mixed, dev_smem, sms);
     if (as != QED_OK) { free_plan(P); return as; }
@@ -557,6 +597,7 @@ qed_status qed_abc_plan_create(const qed_abc_process* proc, qed_precision precis
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc.fn, P->block, P->smem);
   if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
   P->grid = per_sm * sms;
+  P->forms[0] = qed_plan_s::Form{P->kc, P->block, P->grid, P->smem, true, P->team_bytes};
   *out = P;
   return QED_OK;
 }
@@ -654,6 +695,7 @@ qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)P->kc.fn, P->block, P->smem);
   if (e != cudaSuccess || per_sm < 1) { free_plan(P); return e != cudaSuccess ? cuda_status(e) : QED_EUNSUPPORTED; }
   P->grid = per_sm * sms;
+  P->forms[0] = qed_plan_s::Form{P->kc, P->block, P->grid, P->smem, true, P->team_bytes};
   *out = P;
   return QED_OK;
 }
@@ -699,9 +741,87 @@ qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
     info->reduction_steps = P->tp.steps;
   }
   info->team_threads = P->kc.team;
-  info->smem_bytes_per_team = P->team_bytes;
+  info->smem_bytes_per_team = P->forms[P->form.load()].team_bytes;
   info->precision = (int)P->prec;
+  const int f = P->form.load();
+  info->kernel_form = f;
+  info->kernel_forms = (P->forms[0].ok ? 1 : 0) | (P->forms[1].ok ? 2 : 0);
+  info->block_threads = P->forms[f].block;
+  info->grid_blocks = P->forms[f].grid;
   return QED_OK;
+}
+
+qed_status qed_plan_set_kernel_form(qed_plan_t P, int form) {
+  if (!P || form < 0 || form > 1) return QED_EINVAL;
+  if (!P->forms[form].ok) return QED_EUNSUPPORTED;
+  P->form.store(form);
+  return QED_OK;
+}
+
+qed_status qed_plan_tune(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2, void* stream,
+                         int* form, int* block, double* best_ms) {
+  if (!P || n <= 0 || !d_momenta || !d_out_m2 || !aligned8(d_momenta) || !aligned8(d_out_m2))
+    return QED_EINVAL;
+  int sms = 0, dev_smem = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return QED_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return QED_ECUDA; }
+  const int orig = P->form.load();
+  const qed_plan_s::Form saved[2] = {P->forms[0], P->forms[1]};
+  int best_f = orig;
+  qed_plan_s::Form best_cfg = P->forms[orig];
+  double best = 1e300;
+  qed_status s = QED_OK;
+  for (int f = 0; f < 2 && s == QED_OK; ++f) {
+    if (!saved[f].ok) continue;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, (const void*)saved[f].kc.fn) != cudaSuccess) { s = QED_ECUDA; break; }
+    const int team = saved[f].kc.team;
+    for (int blk : {32, 64, 128, 256}) {
+      if (blk < team || blk % team || blk > fa.maxThreadsPerBlock) continue;
+      qed_plan_s::Form c = saved[f];
+      c.block = blk;
+      c.smem = (size_t)(blk / team) * c.team_bytes;
+      if (c.smem > (size_t)dev_smem) continue;
+      if (configure_form(&c, sms) != cudaSuccess) { s = QED_ECUDA; break; }
+      if (!c.ok) continue;
+      P->forms[f] = c;
+      P->form.store(f);
+      s = launch_eval(P, d_momenta, n, d_out_m2, st);   // warm-up
+      if (s != QED_OK) break;
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && s == QED_OK; ++rep) s = launch_eval(P, d_momenta, n, d_out_m2, st);
+      cudaEventRecord(e1, st);
+      if (s != QED_OK || cudaEventSynchronize(e1) != cudaSuccess) { s = s != QED_OK ? s : QED_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 3 < best) { best = ms / 3; best_f = f; best_cfg = c; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->forms[0] = saved[0];
+  P->forms[1] = saved[1];
+  if (s == QED_OK && best < 1e300) {
+    P->forms[best_f] = best_cfg;
+    if (configure_form(&P->forms[best_f], sms) != cudaSuccess) s = QED_ECUDA;
+    P->form.store(best_f);
+  } else {
+    for (int f = 0; f < 2; ++f)
+      if (saved[f].ok) configure_form(&P->forms[f], sms);
+    P->form.store(orig);
+  }
+  if (s == QED_OK) {
+    if (form) *form = best_f;
+    if (block) *block = P->forms[best_f].block;
+    if (best_ms) *best_ms = best;
+  }
+  return s;
 }
 
 qed_status qed_eval(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
@@ -712,14 +832,9 @@ qed_status qed_eval(qed_plan_t P, const double* d_momenta, long long n, double* 
   return launch_eval(P, d_momenta, n, d_out_m2, (cudaStream_t)stream);
 }
 
-qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
-                         double* d_grad, void* stream) {
-  if (!P || n < 0) return QED_EINVAL;
-  if (n == 0) return QED_OK;
-  if (!d_momenta || !d_grad || !aligned8(d_momenta) || !aligned8(d_grad) ||
-      (d_out_m2 && !aligned8(d_out_m2)))
-    return QED_EINVAL;
-  if (!P->has_adj) return QED_EUNSUPPORTED;
+namespace {
+qed_status launch_grad(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2, double* d_grad,
+                       void* scratch, cudaStream_t st) {
   KParams kp = make_params(P, d_momenta, n, d_out_m2);
   kp.grad = d_grad;
   kp.instr = P->d_instr_adj;
@@ -730,15 +845,69 @@ qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, dou
   kp.n_sets = (int)P->sc_adj.sets.size();
   kp.ncur = P->sc_adj.stored_currents + P->sc_adj.local_currents;
   kp.ncur_stored = P->sc_adj.stored_currents;
-  kp.adj_scratch = P->d_adj_scratch;
+  kp.adj_scratch = scratch;
   kp.adj_scratch_team = P->adj_scratch_team;
   kp.part_tab = P->d_part_tab;
   kp.n_part = P->n_part;
   const int tpc = P->block_adj / P->kc_adj.team;
   const long long need = (n + tpc - 1) / tpc;
   const int grid = (int)std::min<long long>(need, P->grid_adj);
-  return cuda_status(launch_forward(P->kc_adj.fn, grid, P->block_adj, P->smem_adj,
-                                    (cudaStream_t)stream, kp));
+  return cuda_status(launch_forward(P->kc_adj.fn, grid, P->block_adj, P->smem_adj, st, kp));
+}
+
+qed_status check_grad_args(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
+                           double* d_grad) {
+  if (!P || n < 0) return QED_EINVAL;
+  if (n == 0) return QED_OK;
+  if (!d_momenta || !d_grad || !aligned8(d_momenta) || !aligned8(d_grad) ||
+      (d_out_m2 && !aligned8(d_out_m2)))
+    return QED_EINVAL;
+  if (!P->has_adj) return QED_EUNSUPPORTED;
+  return QED_OK;
+}
+}  // namespace
+
+qed_status qed_eval_grad(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
+                         double* d_grad, void* stream) {
+  qed_status s = check_grad_args(P, d_momenta, n, d_out_m2, d_grad);
+  if (s != QED_OK || n == 0) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!P->d_adj_scratch) return launch_grad(P, d_momenta, n, d_out_m2, d_grad, nullptr, st);
+  // the plan's scratch: order this launch after the previous one that used
+  // it, whatever its stream (inside a stream capture the ordering is the
+  // capture's own; see qed.h)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (cs != cudaStreamCaptureStatusNone)
+    return launch_grad(P, d_momenta, n, d_out_m2, d_grad, P->d_adj_scratch, st);
+  std::lock_guard<std::mutex> guard(P->scratch_lock);
+  if (P->scratch_used) e = cudaStreamWaitEvent(st, P->ev_scratch, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  s = launch_grad(P, d_momenta, n, d_out_m2, d_grad, P->d_adj_scratch, st);
+  if (s != QED_OK) return s;
+  e = cudaEventRecord(P->ev_scratch, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  P->scratch_used = true;
+  return QED_OK;
+}
+
+qed_status qed_grad_workspace_bytes(qed_plan_t P, long long* bytes) {
+  if (!P || !bytes) return QED_EINVAL;
+  if (!P->has_adj) return QED_EUNSUPPORTED;
+  *bytes = P->d_adj_scratch ? P->adj_scratch_bytes : 0;
+  return QED_OK;
+}
+
+qed_status qed_eval_grad_ws(qed_plan_t P, const double* d_momenta, long long n, double* d_out_m2,
+                            double* d_grad, void* d_workspace, long long workspace_bytes, void* stream) {
+  qed_status s = check_grad_args(P, d_momenta, n, d_out_m2, d_grad);
+  if (s != QED_OK) return s;
+  if (workspace_bytes < 0 || ((uintptr_t)d_workspace & 255u)) return QED_EINVAL;
+  if (P->d_adj_scratch && (!d_workspace || workspace_bytes < P->adj_scratch_bytes)) return QED_EINVAL;
+  if (n == 0) return QED_OK;
+  return launch_grad(P, d_momenta, n, d_out_m2, d_grad, P->d_adj_scratch ? d_workspace : nullptr,
+                     (cudaStream_t)stream);
 }
 
 qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, double* h_out_m2,

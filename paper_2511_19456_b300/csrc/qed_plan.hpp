@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "../../include/qed.h"
@@ -22,6 +23,15 @@ KernelChoice abc_kernel_for(int k, bool mixed, bool rewrite);
 KernelChoice tape_kernel();
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
+// Straight-line specialised forward kernel (generated at build time by
+// qed_codegen.cpp): spin-summed, k = 1..4; fn == nullptr where none exists.
+// ncur and team_bytes: the currents and shared memory per team it expects.
+struct SpecKernel {
+  void (*fn)(const KParams);
+  int team, ncur, team_bytes;
+};
+SpecKernel spec_forward_kernel(int k, bool mixed);
+const char* spec_version();
 }  // namespace qed
 
 using namespace qed;
@@ -39,6 +49,22 @@ struct qed_plan_s {
   int block = 0, grid = 0;
   size_t smem = 0;
   int team_bytes = 0;
+  // Forward kernel forms of a spin-summed plan: [0] the table-driven kernel
+  // above (kc, block, grid, smem: the schedule read from device tables at run
+  // time), [1] the straight-line specialised kernel generated at build time
+  // from the same schedule (with its own shared-memory size per team, which
+  // the generator reports).  The evaluation entry points launch
+  // forms[form]; form is switched by qed_plan_set_kernel_form and
+  // qed_plan_tune.
+  struct Form {
+    KernelChoice kc{nullptr, 0};
+    int block = 0, grid = 0;
+    size_t smem = 0;
+    bool ok = false;
+    int team_bytes = 0;
+  };
+  Form forms[2];
+  std::atomic<int> form{0};
   int fixed_sin = 0, fixed_sout = 0, fixed_pol[8] = {0};
   // adjoint: its own schedule (fewer kept levels where shared memory is short)
   Schedule sc_adj;
@@ -51,6 +77,12 @@ struct qed_plan_s {
   bool has_adj = false;
   void* d_adj_scratch = nullptr;     // global currents/adjoints of the adjoint teams
   long long adj_scratch_team = 0;    // bytes per team
+  long long adj_scratch_bytes = 0;   // the whole scratch (all resident teams)
+  // qed_eval_grad's uses of d_adj_scratch, on any stream, run one after the
+  // other: each launch waits for ev_scratch, recorded after the previous one
+  std::mutex scratch_lock;
+  cudaEvent_t ev_scratch = nullptr;
+  bool scratch_used = false;
   // distributively rewritten DAG (qed_plan_create_rewrite)
   bool rewrite = false;
   // ABC model (qed_abc_plan_create): scalar currents, A and C masses

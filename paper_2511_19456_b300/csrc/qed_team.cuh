@@ -215,7 +215,8 @@ __device__ __forceinline__ double mdot(const double* a, const double* b) {
 // of the FP32 rate) off the critical path where a thread builds several
 // subsets or subsets of many photons (n >= 7); with one subset of few photons
 // per thread the FP64 form is as fast, and it is used there.
-template <int K, typename Real, int TEAM>
+// FORCE_INV: take the invariant-based mixed form whatever the team size.
+template <int K, typename Real, int TEAM, bool FORCE_INV = false>
 __device__ __forceinline__ void point_setup(const KParams& p, int lane, long long ptc, double* s_mom,
                                           Real* s_q, Real* s_eps, Real* s_spin, double* s_w,
                                           float* s_momf) {
@@ -223,7 +224,7 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
   constexpr int NS = K + 3;
   constexpr int NSUB = 1 << N;
   constexpr unsigned ALL = (1u << N) - 1;
-  constexpr bool INV = sizeof(Real) == 4 && (NSUB > TEAM || N >= 7);
+  constexpr bool INV = sizeof(Real) == 4 && (FORCE_INV || NSUB > TEAM || N >= 7);
   // ---- a1: load the point
   for (int i = lane; i < NS * 4; i += TEAM) {
     const double v = __ldg(p.mom + ptc * (NS * 4) + i);

@@ -64,6 +64,8 @@ def test_invalid_arguments_rejected_without_gpu():
     assert L.qed_eval_grad(None, None, 10, None, None, None) == _lib.QED_EINVAL
     assert L.qed_eval_host(None, None, 10, None, None) == _lib.QED_EINVAL
     assert L.qed_plan_info(None, None) == _lib.QED_EINVAL
+    assert L.qed_plan_set_kernel_form(None, 0) == _lib.QED_EINVAL
+    assert L.qed_plan_tune(None, None, 10, None, None, None, None, None) == _lib.QED_EINVAL
     assert L.qed_dag_counts(0, None) == _lib.QED_EINVAL
     L.qed_plan_destroy(None)  # no-op
 
