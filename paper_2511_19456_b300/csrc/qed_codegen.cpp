@@ -31,7 +31,7 @@ namespace {
 
 // Version of the generated kernels (layout, rounds, joins); part of the
 // benchmark's record of which kernel a counter capture belongs to.
-constexpr const char* SPEC_VERSION = "spec-1";
+constexpr const char* SPEC_VERSION = "spec-3";
 
 // One vertex (+ propagation) node of a range.  photon, src and post are C++
 // expressions: literals for the kept currents, entries of the photon set's
@@ -42,6 +42,7 @@ struct Item {
   bool spinor;      // the input is the external spinor (level 1)
   int rank, dst;
   int photon_i, src_i;   // numeric values (kept currents), for sorting and renumbering
+  int leaf_base = -1, leaf_pos = -1;   // leaves: buffer and position, if not the range's own
 };
 
 bool is_int(const std::string& e) {
@@ -148,7 +149,10 @@ struct Emitter {
       rank.push_back(items[i].rank);
       src.push_back(items[i].src);
       pst.push_back(items[i].post);
-      dst.push_back(planar ? i : items[i].dst);
+      // planar: the offset (in reals) of the leaf's chunk (q = 0, s = 0, p = 0)
+      const int lb = items[i].leaf_base >= 0 ? items[i].leaf_base : leaf_base;
+      const int lp = items[i].leaf_pos >= 0 ? items[i].leaf_pos : i;
+      dst.push_back(planar ? lb * 8 + lp * 16 * np : items[i].dst);
       if (items[i].spinor != items[nodes[0]].spinor)
         throw std::runtime_error("spinor and current inputs in one round");
     }
@@ -179,8 +183,7 @@ struct Emitter {
     if (post) o << ind << "const " << real << "* P = s_q + " << per_group(pst) << " * 5;\n";
     else o << ind << "const " << real << "* P = nullptr;\n";
     if (planar) {
-      o << ind << real << "* d0 = s_cur + " << leaf_base * 8 << " + (((" << per_group(dst)
-        << " * 2) * 2 + (v & 1)) * " << np << " + (v >> 1)) * 4;\n";
+      o << ind << real << "* d0 = s_cur + " << per_group(dst) << " + ((v & 1) * " << np << " + (v >> 1)) * 4;\n";
       o << ind << real << "* d1 = d0 + " << 2 * np * 4 << ";\n";
     } else {
       o << ind << real << "* d0 = s_cur + (" << per_group(dst) << " + v) * 8;\n";
@@ -347,8 +350,12 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
   o << "  " << R << "* s_spin = reinterpret_cast<" << R << "*>(base + L.spin);\n";
   o << "  double* s_red = reinterpret_cast<double*>(base + L.red);\n";
   o << "  " << R << "* s_cur = reinterpret_cast<" << R << "*>(base + L.cur);\n";
-  o << "  point_setup<K, " << R << ", TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
-    << "      reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));\n";
+  if (mixed)
+    o << "  spec::setup_f32<K, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
+      << "      reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));\n";
+  else
+    o << "  point_setup<K, double, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
+      << "      reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));\n";
   o << "  Acc<" << R << "> acc[4];\n";
   for (int ph = 0; ph < sc.n_stored_phases; ++ph) {
     o << "  // ---- kept currents, phase " << ph << "\n";
@@ -362,43 +369,88 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
   // its photon and source from the set's row of the constant table.  (One
   // loop body instead of one copy per set: fully unrolled, the k = 4 kernel
   // was 7.6 K instructions per point but stalled on instruction fetch.)
+  //
+  // Where one set's right leaves fill at most half a round, the loop takes
+  // the sets in pairs and builds both sets' right leaves in one round, the
+  // second set's into the currents of the first kept level, which nothing
+  // reads once the second level is built (k = 4: ten sets, 16 right leaf
+  // variants each on 32 lanes).
   const int nsets = (int)sc.sets.size();
   const int leaf_l = sc.stored_currents, leaf_r = sc.stored_currents + NL * (1 << (h + 1));
-  std::vector<Item> lbody = lsets[0], rbody = rsets[0];
-  for (int i = 0; i < NL; ++i) {
-    lbody[i].photon = "cs.lph[" + std::to_string(i) + "]";
-    lbody[i].src = "cs.lsrc[" + std::to_string(i) + "]";
-    lbody[i].post = "0";
-  }
-  for (int i = 0; i < NR; ++i) {
-    rbody[i].photon = "cs.rph[" + std::to_string(i) + "]";
-    rbody[i].src = "cs.rsrc[" + std::to_string(i) + "]";
-    rbody[i].post = "cs.mask";
-  }
+  const int nvr = 1 << (r + 1);
+  int dead_base = -1, dead_size = 0;   // the first left level, once the second is built
+  if (sc.ls >= 2)
+    for (const StoredRange& sr : stored)
+      if (sr.side == 0 && sr.level == 1) {
+        dead_base = sr.items[0].dst;
+        for (const Item& it : sr.items) dead_base = std::min(dead_base, it.dst);
+        dead_size = (int)sr.items.size() * (1 << 2);
+      }
+  const bool paired = 2 * NR * nvr <= team && nsets % 2 == 0 && dead_base >= 0 && dead_size >= NR * nvr;
+  auto left_body = [&](const std::string& t) {
+    std::vector<Item> v = lsets[0];
+    for (int i = 0; i < NL; ++i) {
+      v[i].photon = t + ".lph[" + std::to_string(i) + "]";
+      v[i].src = t + ".lsrc[" + std::to_string(i) + "]";
+      v[i].post = "0";
+    }
+    return v;
+  };
+  auto right_body = [&](const std::string& t, int base) {
+    std::vector<Item> v = rsets[0];
+    for (int i = 0; i < NR; ++i) {
+      v[i].photon = t + ".rph[" + std::to_string(i) + "]";
+      v[i].src = t + ".rsrc[" + std::to_string(i) + "]";
+      v[i].post = t + ".mask";
+      v[i].leaf_base = base;
+      v[i].leaf_pos = i;
+    }
+    return v;
+  };
+  auto emit_rounds = [&](const std::vector<std::string>& rs) { for (const std::string& x : rs) o << x; };
+  auto join = [&](const std::string& set_index, int rbase) {
+    o << "    {\n";
+    o << "      const unsigned tv = __ldg(p.lane_tab + ((" << set_index << ") << " << n
+      << ") + lane);   // pext(lane, S) | pext(lane, ~S) << 8\n";
+    o << "      const int pl = (int)(tv & 0xffu), pr = (int)(tv >> 8);\n";
+    if (mixed)
+      o << "      spec::join_set_f32<" << NL << ", " << NR << ", " << NPL << ", " << NPR
+        << ">(reinterpret_cast<const float4*>(s_cur + " << leaf_l * 8 << ") + pl,\n"
+        << "          reinterpret_cast<const float4*>(s_cur + " << rbase * 8 << ") + pr, acc);\n";
+    else
+      o << "      spec::join_set_f64<" << NL << ", " << NR << ", " << NPL << ", " << NPR << ">(s_cur + " << leaf_l * 8
+        << " + pl * 4, s_cur + " << rbase * 8 << " + pr * 4, acc);\n";
+    o << "    }\n";
+    o << "    team_sync<TEAM>();\n";
+  };
+  const std::string TT = "spec::SetTable<" + std::to_string(NL) + ", " + std::to_string(NR) + ">";
   o << "  // ---- the " << nsets << " photon sets S (|S| = " << h << "): leaves, then the joins of "
-    << NL * NR << " diagrams x 4 states per lane\n";
+    << NL * NR << " diagrams x 4 states per lane" << (paired ? "; sets in pairs" : "") << "\n";
   o << "#pragma unroll 1\n";
-  o << "  for (int s = 0; s < " << nsets << "; ++s) {\n";
-  o << "    const spec::SetTable<" << NL << ", " << NR << ">& cs = " << tab << "[s];\n";
   em.indent = "    ";
-  for (const std::string& x : em.rounds(lbody, 0, h, post_of(P0, lslot), true, leaf_l, NPL, "left leaves")) o << x;
-  for (const std::string& x : em.rounds(rbody, 1, r, post_of(P0, rslot), true, leaf_r, NPR,
-                                        "right leaves (S2 propagation hoisted)"))
-    o << x;
+  if (!paired) {
+    o << "  for (int s = 0; s < " << nsets << "; ++s) {\n";
+    o << "    const " << TT << "& cs = " << tab << "[s];\n";
+    emit_rounds(em.rounds(left_body("cs"), 0, h, false, true, leaf_l, NPL, "left leaves"));
+    emit_rounds(em.rounds(right_body("cs", leaf_r), 1, r, true, true, leaf_r, NPR,
+                          "right leaves (S2 propagation hoisted)"));
+    o << "    team_sync<TEAM>();\n";
+    join("s", leaf_r);
+  } else {
+    o << "  for (int s = 0; s < " << nsets << "; s += 2) {\n";
+    o << "    const " << TT << "& ca = " << tab << "[s];\n";
+    o << "    const " << TT << "& cb = " << tab << "[s + 1];\n";
+    std::vector<Item> rr = right_body("ca", leaf_r);
+    for (const Item& it : right_body("cb", dead_base)) rr.push_back(it);
+    emit_rounds(em.rounds(rr, 1, r, true, true, leaf_r, NPR, "right leaves of both sets (S2 propagation hoisted)"));
+    emit_rounds(em.rounds(left_body("ca"), 0, h, false, true, leaf_l, NPL, "left leaves, first set"));
+    o << "    team_sync<TEAM>();\n";
+    join("s", leaf_r);
+    emit_rounds(em.rounds(left_body("cb"), 0, h, false, true, leaf_l, NPL, "left leaves, second set"));
+    o << "    team_sync<TEAM>();\n";
+    join("s + 1", dead_base);
+  }
   em.indent = "  ";
-  o << "    team_sync<TEAM>();\n";
-  o << "    {\n";
-  o << "      const unsigned tv = __ldg(p.lane_tab + (s << " << n << ") + lane);   // pext(lane, S) | pext(lane, ~S) << 8\n";
-  o << "      const int pl = (int)(tv & 0xffu), pr = (int)(tv >> 8);\n";
-  if (mixed)
-    o << "      spec::join_set_f32<" << NL << ", " << NR << ", " << NPL << ", " << NPR
-      << ">(reinterpret_cast<const float4*>(s_cur + " << leaf_l * 8 << ") + pl,\n"
-      << "          reinterpret_cast<const float4*>(s_cur + " << leaf_r * 8 << ") + pr, acc);\n";
-  else
-    o << "      spec::join_set_f64<" << NL << ", " << NR << ", " << NPL << ", " << NPR << ">(s_cur + " << leaf_l * 8
-      << " + pl * 4, s_cur + " << leaf_r * 8 << " + pr * 4, acc);\n";
-  o << "    }\n";
-  o << "    team_sync<TEAM>();\n";
   o << "  }\n";
   o << "  spec::finish_summed<TEAM>(p, acc, lane, pt, valid, s_red);\n";
   o << "  team_sync<TEAM>();\n";

@@ -19,16 +19,17 @@ namespace qed {
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 
-// Helicity spinor u(p, h) in precision T from the FP64 momentum p:
+// Helicity spinor u(p, h) in precision T:
 // u = (sqrt(E+m) chi, h sqrt(E-m) chi), chi_+ = (|p|+pz, px + i py)/N,
 // chi_- = (-px + i py, |p|+pz)/N, N = sqrt(2|p|(|p|+pz)); |p| = 0 uses the
 // z axis, |p|+pz = 0 gives chi_+ = (0, 1), chi_- = (-1, 0).
-// bar: ubar = u^dagger gamma^0.  E +- m are formed in FP64.  In FP32, |p|+pz
-// is formed as (px^2 + py^2)/(|p| - pz) when pz < 0 (the same quantity
-// without the cancellation near the -z axis).
+// bar: ubar = u^dagger gamma^0.  In FP32, |p|+pz is formed as
+// (px^2 + py^2)/(|p| - pz) when pz < 0 (the same quantity without the
+// cancellation near the -z axis).  make_spinor_core takes px, py, pz and
+// E + m, E - m already in precision T; make_spinor forms them from the FP64
+// momentum (E +- m in FP64).
 template <typename T>
-__device__ __forceinline__ void make_spinor(const double* p, int hbit, double m, bool bar, T out[8]) {
-  const T px = (T)p[1], py = (T)p[2], pz = (T)p[3];
+__device__ __forceinline__ void make_spinor_core(T px, T py, T pz, T epm, T emm, int hbit, bool bar, T out[8]) {
   const T pt2 = px * px + py * py;
   const T ap = sqrt_t(pt2 + pz * pz);
   T c0r, c0i, c1r, c1i;
@@ -46,8 +47,8 @@ __device__ __forceinline__ void make_spinor(const double* p, int hbit, double m,
       else       { c0r = -px / nrm; c0i = py / nrm; c1r = apz / nrm; c1i = (T)0; }
     }
   }
-  const T a = sqrt_t((T)(p[0] + m));
-  const T bb = (T)(p[0] - m);
+  const T a = sqrt_t(epm);
+  const T bb = emm;
   T b = bb > (T)0 ? sqrt_t(bb) : (T)0;
   if (hbit) b = -b;
   const T u[8] = {a * c0r, a * c0i, a * c1r, a * c1i, b * c0r, b * c0i, b * c1r, b * c1i};
@@ -60,11 +61,15 @@ __device__ __forceinline__ void make_spinor(const double* p, int hbit, double m,
     out[4] = -u[4]; out[5] = u[5]; out[6] = -u[6]; out[7] = u[7];
   }
 }
-
-// Real linear polarisation 3-vector (eps^0 = 0) of a photon with momentum k.
 template <typename T>
-__device__ __forceinline__ void make_pol(const double* k, int pbit, T e[3]) {
-  const T kx = (T)k[1], ky = (T)k[2], kz = (T)k[3];
+__device__ __forceinline__ void make_spinor(const double* p, int hbit, double m, bool bar, T out[8]) {
+  make_spinor_core<T>((T)p[1], (T)p[2], (T)p[3], (T)(p[0] + m), (T)(p[0] - m), hbit, bar, out);
+}
+
+// Real linear polarisation 3-vector (eps^0 = 0) of a photon with momentum
+// components (kx, ky, kz) in precision T.
+template <typename T>
+__device__ __forceinline__ void make_pol_core(T kx, T ky, T kz, int pbit, T e[3]) {
   const T kt2 = kx * kx + ky * ky;
   if (kt2 == (T)0) {
     e[0] = pbit ? (T)0 : (T)1; e[1] = pbit ? (T)1 : (T)0; e[2] = (T)0;
@@ -77,6 +82,11 @@ __device__ __forceinline__ void make_pol(const double* k, int pbit, T e[3]) {
   } else {
     e[0] = -ky / kt; e[1] = kx / kt; e[2] = (T)0;
   }
+}
+// ... of a photon with FP64 momentum k.
+template <typename T>
+__device__ __forceinline__ void make_pol(const double* k, int pbit, T e[3]) {
+  make_pol_core<T>((T)k[1], (T)k[2], (T)k[3], pbit, e);
 }
 
 // Propagator of the line carrying photon set `mask`: Q = p + sum c_j k_j

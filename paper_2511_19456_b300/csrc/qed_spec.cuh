@@ -88,6 +88,146 @@ __device__ __forceinline__ void ld3(const double* e, double ev[3]) {
   ev[0] = a.x; ev[1] = a.y; ev[2] = e[2];
 }
 
+// ------------------------------------------------------------ set-up
+// Per point, FP32-mixed (a1-a3 for a team of one lane per photon subset,
+// TEAM = 2^n, k <= 4): the momenta, the propagator entries of every subset
+// and the external states, with as few FP64 instructions as the method
+// allows (each occupies B300's FP64 pipe for a warp's worth of lanes; this
+// set-up needs about 15 per point where the direct form needs about 45).
+//   1. each lane loads one FP64 momentum component and splits it into a
+//      float-float pair (hi + lo, exact to about 2^-48);
+//   2. the Lorentz invariants, one Minkowski product per lane in FP64:
+//      p.p, p'.p', k_j.k_j, p.k_j, p'.k_j and k_i.k_j (i < j), with the
+//      photon slots k_0 = incoming, k_j (j >= 1) outgoing;
+//   3. for the subset T of each lane, the FP64 denominator as the same sum
+//      as Q_T^2 - m^2 in invariants.  With |T| <= n/2 the line is taken
+//      from the incoming electron, Q_T = p + sum_{j in T} sigma_j k_j
+//      (sigma_0 = +1, sigma_j = -1); otherwise from the outgoing electron,
+//      Q_T = p' - sum_{j not in T} sigma_j k_j, which is the same momentum
+//      by momentum conservation.  With U the photons summed (at most two)
+//      and tau = sigma (incoming side) or -sigma (outgoing side),
+//        D_T = (q.q - m^2) + sum_{j in U} (k_j.k_j + 2 tau_j q.k_j)
+//              + sum_{i<j in U} 2 tau_i tau_j k_i.k_j,   q = p or p';
+//      the numerator Q_T in float-float (TwoSum on the FP32 pipe), rounded
+//      once; the entries (Q0 +- m)/D and Q/D in FP32;
+//   4. u(p, +-), ubar(p', +-) and eps_j (pol 1, 2) in FP32 from the
+//      float-float momenta (E +- m as float-float sums rounded once).
+// Missing photons of U read a zero slot, so every lane runs the same code.
+template <int N>
+__device__ __forceinline__ int photon_slot(int j) { return j == 0 ? 1 : j + 2; }
+
+template <int N>
+__device__ __forceinline__ int pair_index(int i, int j) {   // i < j: k_i.k_j in the product table
+  return 2 + 3 * N + (i * (2 * N - i - 1)) / 2 + (j - i - 1);
+}
+
+template <int K, int TEAM>
+__device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long pt, double* s_mom, float* s_q,
+                                          float* s_eps, float* s_spin, double* s_w, float* s_momf) {
+  constexpr int N = K + 1, NS = K + 3, NC = NS * 4;
+  constexpr unsigned ALL = (1u << N) - 1;
+  constexpr int NPROD = 2 + 3 * N + N * (N - 1) / 2;
+  static_assert((1 << N) == TEAM, "one lane per photon subset");
+  static_assert(N / 2 <= 2, "at most two photons per denominator");
+  // 1. momenta (FP64) and their float-float split
+  for (int i = lane; i < NC; i += TEAM) {
+    const double v = __ldg(p.mom + pt * NC + i);
+    const float hi = (float)v;
+    s_mom[i] = v;
+    s_momf[i] = hi;
+    s_momf[NC + i] = (float)(v - (double)hi);
+  }
+  if (lane == 0) s_w[NPROD] = 0.0;
+  team_sync<TEAM>();
+  // 2. the invariants
+  for (int it = lane; it < NPROD; it += TEAM) {
+    int a, b;
+    if (it < 2) {
+      a = b = it == 0 ? 0 : 2;
+    } else if (it < 2 + N) {
+      a = b = photon_slot<N>(it - 2);
+    } else if (it < 2 + 3 * N) {
+      a = it < 2 + 2 * N ? 0 : 2;
+      b = photon_slot<N>((it - 2) % N);
+    } else {
+      int r = it - 2 - 3 * N, i = 0;
+      while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
+      a = photon_slot<N>(i);
+      b = photon_slot<N>(i + 1 + r);
+    }
+    s_w[it] = mdot(s_mom + 4 * a, s_mom + 4 * b);
+  }
+  team_sync<TEAM>();
+  // 3. the subset of this lane
+  {
+    const unsigned T = (unsigned)lane;
+    float* d = s_q + T * 5;
+    const bool out = 2 * __popc(T) > N;
+    const unsigned U = out ? ALL & ~T : T;
+    const int ja = U ? __ffs(U) - 1 : -1;
+    const unsigned U2 = U & (U - 1);
+    const int jb = U2 ? __ffs(U2) - 1 : -1;
+    // tau_j: sigma_j on the incoming side, -sigma_j on the outgoing side
+    const double sa = ja < 0 ? 0.0 : ((ja == 0) != out ? 1.0 : -1.0);
+    const double sb = jb < 0 ? 0.0 : ((jb == 0) != out ? 1.0 : -1.0);
+    const int qk0 = out ? 2 + 2 * N : 2 + N;
+    const double m = p.mass;
+    double D = fma(-m, m, s_w[out ? 1 : 0]);
+    D += s_w[ja < 0 ? NPROD : 2 + ja];
+    D = fma(2.0 * sa, s_w[ja < 0 ? NPROD : qk0 + ja], D);
+    D += s_w[jb < 0 ? NPROD : 2 + jb];
+    D = fma(2.0 * sb, s_w[jb < 0 ? NPROD : qk0 + jb], D);
+    D = fma(2.0 * sa * sb, s_w[jb < 0 ? NPROD : pair_index<N>(ja, jb)], D);
+    // the numerator in float-float: q + tau_a k_a + tau_b k_b
+    const int qs = out ? 2 : 0;
+    const int ka = photon_slot<N>(ja < 0 ? 0 : ja), kb = photon_slot<N>(jb < 0 ? 0 : jb);
+    const float ta = (float)sa, tb = (float)sb;
+    float qh[4], ql[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float sum, err;
+      qh[c] = s_momf[qs * 4 + c];
+      ql[c] = s_momf[NC + qs * 4 + c];
+      two_sum_f(qh[c], ta * s_momf[ka * 4 + c], sum, err);
+      qh[c] = sum;
+      ql[c] = __fadd_rn(ql[c], __fadd_rn(err, ta * s_momf[NC + ka * 4 + c]));
+      two_sum_f(qh[c], tb * s_momf[kb * 4 + c], sum, err);
+      qh[c] = sum;
+      ql[c] = __fadd_rn(ql[c], __fadd_rn(err, tb * s_momf[NC + kb * 4 + c]));
+    }
+    const bool used = T != 0 && T != ALL;
+    const float inv = used ? 1.0f / (float)D : 0.0f;
+    const float mf = (float)m;
+    // Q0 -+ m: the high part first (exact where Q0 is close to m)
+    d[0] = __fadd_rn(__fadd_rn(qh[0], mf), ql[0]) * inv;
+    d[1] = __fadd_rn(__fsub_rn(qh[0], mf), ql[0]) * inv;
+    d[2] = __fadd_rn(qh[1], ql[1]) * inv;
+    d[3] = __fadd_rn(qh[2], ql[2]) * inv;
+    d[4] = __fadd_rn(qh[3], ql[3]) * inv;
+  }
+  // 4. external states in FP32
+  for (int it = lane; it < 4 + 2 * N; it += TEAM) {
+    if (it < 4) {
+      const int side = it >> 1, e = it & 1;
+      const float* h = s_momf + (side ? 8 : 0);
+      const float* l = s_momf + NC + (side ? 8 : 0);
+      const float mf = (float)p.mass;
+      float sp[8];
+      make_spinor_core<float>(h[1], h[2], h[3], __fadd_rn(__fadd_rn(h[0], mf), l[0]),
+                              __fadd_rn(__fsub_rn(h[0], mf), l[0]), e, side == 1, sp);
+      store8(s_spin + (side * 2 + e) * 8, sp);
+    } else {
+      const int j = (it - 4) >> 1, pb = (it - 4) & 1;
+      const float* h = s_momf + 4 * photon_slot<N>(j);
+      float ev[3];
+      make_pol_core<float>(h[1], h[2], h[3], pb, ev);
+      float* d = s_eps + (j * 2 + pb) * 4;
+      d[0] = ev[0]; d[1] = ev[1]; d[2] = ev[2]; d[3] = 0.f;
+    }
+  }
+  team_sync<TEAM>();
+}
+
 // One vertex item (task V), optionally followed by its propagation (task S1,
 // or the propagation half of S2 that is hoisted onto a right leaf):
 //   side 0 (column current):  z = [S(Q)] eps/ x
@@ -121,24 +261,27 @@ __device__ __forceinline__ void vs_item(const Real* xs, const Real* e, const Rea
 // (leaf layout above; NPL, NPR patterns).
 //
 // Packed FP32 FMAs (two lanes of arithmetic per instruction): with
-// L_c = (lr, li) and R_c = (rr, ri),
-//   A += (lr, lr) * (rr, ri),  B += (li, li) * (rr, ri)
-// so that A = (sum lr rr, sum lr ri), B = (sum li rr, sum li ri) and
+// L_c = (lr, li) and R_c = (rr, ri), the right leaves held in registers as
+// (rr, rr) and (ri, ri) for the whole set,
+//   A += (rr, rr) * (lr, li),  B += (ri, ri) * (lr, li)
+// so that A = (sum rr lr, sum rr li), B = (sum ri lr, sum ri li) and
 //   Re M = A.x - B.y,  Im M = A.y + B.x.
 // A starts from minus the accumulator's compensation (the first step of the
 // Kahan update), B from zero.
 template <int NL, int NR, int NPL, int NPR>
 __device__ __forceinline__ void join_set_f32(const float4* L, const float4* R, Acc<float> acc[4]) {
-  float2 r[NR][2][4];
+  float2 rr[NR][2][4], ri[NR][2][4];
 #pragma unroll
   for (int b = 0; b < NR; ++b)
 #pragma unroll
     for (int so = 0; so < 2; ++so) {
       const float4 c0 = R[((b * 2 + 0) * 2 + so) * NPR], c1 = R[((b * 2 + 1) * 2 + so) * NPR];
-      r[b][so][0] = make_float2(c0.x, c0.y);
-      r[b][so][1] = make_float2(c0.z, c0.w);
-      r[b][so][2] = make_float2(c1.x, c1.y);
-      r[b][so][3] = make_float2(c1.z, c1.w);
+      const float re[4] = {c0.x, c0.z, c1.x, c1.z}, im[4] = {c0.y, c0.w, c1.y, c1.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        rr[b][so][c] = make_float2(re[c], re[c]);
+        ri[b][so][c] = make_float2(im[c], im[c]);
+      }
     }
   float2 A[2][2], B[2][2];
 #pragma unroll
@@ -150,27 +293,26 @@ __device__ __forceinline__ void join_set_f32(const float4* L, const float4* R, A
     }
 #pragma unroll
   for (int a = 0; a < NL; ++a) {
-    float lr[2][4], li[2][4];
+    float2 l[2][4];
 #pragma unroll
     for (int si = 0; si < 2; ++si) {
       const float4 c0 = L[((a * 2 + 0) * 2 + si) * NPL], c1 = L[((a * 2 + 1) * 2 + si) * NPL];
-      lr[si][0] = c0.x; li[si][0] = c0.y; lr[si][1] = c0.z; li[si][1] = c0.w;
-      lr[si][2] = c1.x; li[si][2] = c1.y; lr[si][3] = c1.z; li[si][3] = c1.w;
+      l[si][0] = make_float2(c0.x, c0.y);
+      l[si][1] = make_float2(c0.z, c0.w);
+      l[si][2] = make_float2(c1.x, c1.y);
+      l[si][3] = make_float2(c1.z, c1.w);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int si = 0; si < 2; ++si) {
-        const float2 br = make_float2(lr[si][c], lr[si][c]);
-        const float2 bi = make_float2(li[si][c], li[si][c]);
+      for (int si = 0; si < 2; ++si)
 #pragma unroll
         for (int b = 0; b < NR; ++b)
 #pragma unroll
           for (int so = 0; so < 2; ++so) {
-            A[si][so] = __ffma2_rn(br, r[b][so][c], A[si][so]);
-            B[si][so] = __ffma2_rn(bi, r[b][so][c], B[si][so]);
+            A[si][so] = __ffma2_rn(rr[b][so][c], l[si][c], A[si][so]);
+            B[si][so] = __ffma2_rn(ri[b][so][c], l[si][c], B[si][so]);
           }
-      }
   }
 #pragma unroll
   for (int si = 0; si < 2; ++si)

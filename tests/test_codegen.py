@@ -36,18 +36,31 @@ def expected_rounds(k):
     stored = sum(rounds_of(ph["cnt"][s], ph["level"][s], team)
                  for ph in sc["phases"][: sc["n_stored_phases"]] for s in range(2) if ph["cnt"][s])
     ph = sc["phases"][sc["sets"][0]["phase0"]]
-    per_set = sum(rounds_of(ph["cnt"][s], ph["level"][s], team) for s in range(2) if ph["cnt"][s])
-    return stored, per_set, sc
+    n_sets = len(sc["sets"])
+    side = {s: int(sc["instr"][ph["beg"][s]]["side"]) for s in range(2) if ph["cnt"][s]}
+    left = [s for s in side if side[s] == 0]
+    right = [s for s in side if side[s] == 1]
+    lr = rounds_of(ph["cnt"][left[0]], ph["level"][left[0]], team)
+    nr, rlev = ph["cnt"][right[0]], ph["level"][right[0]]
+    # sets in pairs where one set's right leaves fill at most half a round and
+    # the first left level is free once the second is kept (ls >= 2)
+    paired = 2 * nr * (1 << (rlev + 1)) <= team and n_sets % 2 == 0 and sc["ls"] >= 2
+    if paired:
+        per_body = 2 * lr + rounds_of(2 * nr, rlev, team)
+    else:
+        per_body = lr + rounds_of(nr, rlev, team)
+    return stored, per_body, sc, paired
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("real", ["f32", "f64"])
 def test_rounds_follow_the_schedule(generated, k, real):
     body = kernel_body(generated, k, real)
-    stored, per_set, sc = expected_rounds(k)
-    assert body.count("spec::vs_item<") == stored + per_set
-    assert body.count("spec::join_set_") == 1
-    assert f"for (int s = 0; s < {len(sc['sets'])}; ++s)" in body
+    stored, per_body, sc, paired = expected_rounds(k)
+    assert body.count("spec::vs_item<") == stored + per_body
+    assert body.count("spec::join_set_") == (2 if paired else 1)
+    assert f"for (int s = 0; s < {len(sc['sets'])}; {'s += 2' if paired else '++s'})" in body
+    assert paired == (k == 4)
     # nothing is read from instruction tables at run time
     assert "p.instr" not in body and "ld_instr" not in body
 
