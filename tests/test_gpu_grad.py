@@ -84,8 +84,8 @@ def test_fixed_state_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
     """One fixed spin state, mixed precision: FP32 currents, adjoints and
     parameter terms, with the terms of one photon set summed in FP32 before
     they are added to the FP64 accumulators.  Bound per point, relative to
-    max|g_ref|: the forward mixed bound 32 (2n - 1) u32 max(kappa, 1)."""
-    from tests.test_gpu_parity import mixed_tol
+    max|g_ref|: the per-step bound 32 (2n - 1) u32 max(kappa, 1)."""
+    from tests.test_gpu_parity import mixed_step_tol
     mom = ps.points(k, npts, 1.0 + k, seed=630 + k)
     hel = fixed_hel(k)
     _, g = gpu_grad(Plan(k, summed=False, hel=hel, precision="mixed"), mom)
@@ -94,7 +94,7 @@ def test_fixed_state_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
     err = np.abs(g - ref_g).max(axis=(1, 2)) / np.abs(ref_g).max(axis=(1, 2))
     print(f"\nfixed mixed adjoint k={k}: grad max rel err {err.max():.3e} median {np.median(err):.3e} "
           f"(kappa max {kap.max():.1f})")
-    assert np.all(err <= mixed_tol(k, kap)), (err.max(), int(err.argmax()))
+    assert np.all(err <= mixed_step_tol(k, kap)), (err.max(), int(err.argmax()))
 
 
 @pytest.mark.parametrize("k,summed,npts", [(3, True, 64), (4, True, 32), (5, False, 64), (6, False, 64)])
@@ -102,8 +102,9 @@ def test_fixed_state_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
 def test_adjoint_m2_vs_oracle(orc, k, summed, npts, precision):
     """|M|^2 from the adjoint (spin-summed: each photon set joined through its
     leaf sums, one dot per state; one fixed state: per-diagram joins) meets
-    the forward kernels' bounds."""
-    from tests.test_gpu_parity import fp64_tol, mixed_tol
+    the FP64 bound, and in mixed precision the per-step bound (leaf sums add
+    currents before the product)."""
+    from tests.test_gpu_parity import fp64_tol, mixed_step_tol
     mom = ps.points(k, npts, 1.0 + k, seed=640 + k)
     hel = None if summed else fixed_hel(k)
     mask = orc.all_summed(k) if summed else 0
@@ -111,18 +112,19 @@ def test_adjoint_m2_vs_oracle(orc, k, summed, npts, precision):
     ref, kap = orc.m2(mom, sum_mask=mask, hel=hel, kappa=True)
     rel = np.abs(m2 / ref - 1.0)
     print(f"\nadjoint |M|^2 k={k} summed={summed} {precision}: max rel {rel.max():.3e}")
-    assert np.all(rel <= (fp64_tol(kap) if precision == "fp64" else mixed_tol(k, kap)))
+    assert np.all(rel <= (fp64_tol(kap) if precision == "fp64" else mixed_step_tol(k, kap)))
 
 
 @pytest.mark.parametrize("k,npts", [(1, 64), (2, 64), (3, 32), (4, 16), (5, 4)])
 def test_summed_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
     """All spin states, mixed precision (FP32 parameter terms summed per
-    photon set before the FP64 accumulators): the forward mixed bound.  The
+    photon set before the FP64 accumulators): the per-step bound
+    32 (2n - 1) u32 max(kappa, 1).  The
     error is taken relative to the gradient's natural scale per point,
     max(max|g_ref|, |M|^2 / min_j |k_j|): where |M|^2 is near stationary in
     some k_j, the FP32 rounding of its terms stays of order u32 |M|^2 / |k|
     while the gradient itself vanishes."""
-    from tests.test_gpu_parity import mixed_tol
+    from tests.test_gpu_parity import mixed_step_tol
     mom = ps.points(k, npts, 1.0 + k, seed=660 + k)
     _, g = gpu_grad(Plan(k, precision="mixed"), mom)
     ref_m2, ref_g = orc.grad(mom, sum_mask=orc.all_summed(k))
@@ -133,7 +135,7 @@ def test_summed_mixed_adjoint_vs_oracle_gradient(orc, k, npts):
     w = int(err.argmax())
     print(f"\nsummed mixed adjoint k={k}: grad max rel err {err.max():.3e} median {np.median(err):.3e} "
           f"(worst point: max|g| {gmax[w]:.3e}, |M|^2/|k|min {ref_m2[w] / kmin[w]:.3e})")
-    assert np.all(err <= mixed_tol(k, kap)), (err.max(), w)
+    assert np.all(err <= mixed_step_tol(k, kap)), (err.max(), w)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -141,7 +143,7 @@ def test_k7_fixed_state_adjoint_vs_oracle_gradient(orc, precision):
     """k = 7 (40,320 diagrams), one fixed state: the FP64 form allows 255
     registers per thread and the mixed form keeps one level fewer, with
     several partial-sum slots per photon set."""
-    from tests.test_gpu_parity import fp64_tol, mixed_tol
+    from tests.test_gpu_parity import fp64_tol, mixed_step_tol
     k = 7
     mom = ps.points(k, 32, 8.0, seed=650)
     hel = fixed_hel(k)
@@ -156,8 +158,8 @@ def test_k7_fixed_state_adjoint_vs_oracle_gradient(orc, precision):
         assert np.all(err <= np.maximum(1e-10, 64 * U64 * kap))
         assert np.all(rel <= fp64_tol(kap))
     else:
-        assert np.all(err <= mixed_tol(k, kap))
-        assert np.all(rel <= mixed_tol(k, kap))
+        assert np.all(err <= mixed_step_tol(k, kap))
+        assert np.all(rel <= mixed_step_tol(k, kap))
 
 
 def test_autograd_function():

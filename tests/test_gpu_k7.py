@@ -8,7 +8,7 @@ import pytest
 
 from paper_2511_19456_b300 import Plan
 from tests.golden.make_golden import load_k7
-from tests.test_gpu_parity import MIXED_MEDIAN_TOL
+from tests.test_gpu_parity import check_mixed_median, mixed_step_tol, mixed_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -24,10 +24,10 @@ def test_k7_summed_vs_stored_oracle(precision):
     rel = np.abs(got / ref - 1.0)
     print(f"\nk=7 summed {precision}: max rel {rel.max():.3e} median {np.median(rel):.3e} "
           f"(kappa max {kap.max():.1f})")
-    tol = np.maximum(1e-12, 64 * U64 * kap) if precision == "fp64" else 32 * 15 * U32 * np.maximum(kap, 1)
+    tol = np.maximum(1e-12, 64 * U64 * kap) if precision == "fp64" else mixed_tol(7, kap)
     assert np.all(rel <= tol)
     if precision == "mixed":
-        assert np.median(rel) <= MIXED_MEDIAN_TOL
+        check_mixed_median(rel, kap)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -38,7 +38,7 @@ def test_k7_adjoint_m2_vs_stored_oracle(precision):
     m2, _ = Plan(7, precision=precision).eval_grad(torch.from_numpy(mom).cuda())
     rel = np.abs(m2.cpu().numpy() / ref - 1.0)
     print(f"\nk=7 adjoint |M|^2 {precision}: max rel {rel.max():.3e} median {np.median(rel):.3e}")
-    tol = np.maximum(1e-12, 64 * U64 * kap) if precision == "fp64" else 32 * 15 * U32 * np.maximum(kap, 1)
+    tol = np.maximum(1e-12, 64 * U64 * kap) if precision == "fp64" else mixed_step_tol(7, kap)
     assert np.all(rel <= tol)
 
 

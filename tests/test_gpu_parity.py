@@ -8,11 +8,24 @@ the oracle's measure of cancellation among the diagrams:
   (the oracle's included), so where kappa exceeds ~1e2 the 1e-12 target is
   replaced by the rounding bound.
 * Mixed path (FP32 currents, Kahan-compensated diagram sums; FP64 momenta,
-  denominators, spin sum): relative error <= 32 (2n-1) u32 max(kappa, 1),
-  u32 = 2^-24: 2n-1 rounded matrix-vector steps per diagram, each of which
-  can lose a few bits where a propagator is close to its pole, and the
-  diagram cancellation kappa; the median must stay below 4e-6.  Median and
-  maximum are printed.
+  denominators, spin sum): relative error <= C_MIX u32 max(kappa, 1),
+  u32 = 2^-24, C_MIX = 64, and the median of z = rel / (u32 max(kappa, 1))
+  <= 2.  Error model: every diagram amplitude is formed in FP32 with an
+  error of a few u32 |A_d|; the errors of the diagrams add (at worst
+  linearly) into each state's amplitude, so the error of |M|^2 relative to
+  |M|^2 is a few u32 times kappa, independent of the number of steps.  A
+  propagator close to its pole adds a rare tail that kappa does not
+  measure.  The constant is calibrated on B300 against the oracle: on
+  16,384 points per spin-summed k = 1..4, 2,048 at k = 5, 256 at k = 6, and
+  8,192 / 4,096 points of one fixed state at k = 4 / 6, the largest z was
+  7.6 (summed) and 14.4 (fixed state, kappa up to 2.9e3), the medians 0.15
+  to 0.94; over every mixed comparison of the GPU tests (both kernel forms,
+  all configurations) the largest z was 33, at one of 70,001 k = 4 points
+  (kappa 6.4), and the largest median 1.2.  C_MIX is twice the largest
+  error seen; the median bound catches a loss spread over all points.
+* Gradients and the |M|^2 of the adjoint's own forward pass (its leaf-sum
+  joins add currents before the product, not diagrams) keep the per-step
+  rounding bound 32 (2n-1) u32 max(kappa, 1) (mixed_step_tol).
 """
 import math
 
@@ -33,10 +46,28 @@ def fp64_tol(kappa):
     return np.maximum(FP64_TOL, 64 * U64 * kappa)
 
 
-MIXED_MEDIAN_TOL = 4e-6
+C_MIX = 64
+MIXED_MEDIAN_Z = 2.0
 
 
 def mixed_tol(k, kappa):
+    """Per-point bound of the mixed forward |M|^2 (k kept for the callers)."""
+    return C_MIX * U32 * np.maximum(kappa, 1.0)
+
+
+def mixed_z(rel, kappa):
+    return rel / (U32 * np.maximum(kappa, 1.0))
+
+
+def check_mixed_median(rel, kappa):
+    z = mixed_z(rel, kappa)
+    print(f"  mixed z = rel / (u32 max(kappa, 1)): median {np.median(z):.2f} max {z.max():.2f}")
+    assert np.median(z) <= MIXED_MEDIAN_Z
+
+
+def mixed_step_tol(k, kappa):
+    """Per-step rounding bound, 2n-1 FP32 steps per diagram: gradients and the
+    adjoint's own |M|^2."""
     return 32 * (2 * (k + 1) - 1) * U32 * np.maximum(kappa, 1.0)
 
 # (k, summed, omega, points compared with the oracle)
@@ -80,7 +111,7 @@ def test_parity_vs_oracle(orc, k, summed, omega, npts, precision):
     bad = np.nonzero(rel > tol)[0]
     assert bad.size == 0, (bad[:5], rel[bad[:5]], kap[bad[:5]])
     if precision == "mixed":
-        assert np.median(rel) <= MIXED_MEDIAN_TOL
+        check_mixed_median(rel, kap)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 127, 1000, 4099])
@@ -127,7 +158,7 @@ def test_full_size_k4_sampled(orc, precision):
     tol = fp64_tol(kap) if precision == "fp64" else mixed_tol(4, kap)
     assert np.all(rel <= tol)
     if precision == "mixed":
-        assert np.median(rel) <= MIXED_MEDIAN_TOL
+        check_mixed_median(rel, kap)
 
 
 def test_photon_permutation_invariance_full_size(orc):

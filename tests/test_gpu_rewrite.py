@@ -13,7 +13,7 @@ import pytest
 
 from paper_2511_19456_b300 import Plan, phasespace as ps
 from tests.golden.make_golden import load_k7
-from tests.test_gpu_parity import fixed_hel, fp64_tol, mixed_tol, MIXED_MEDIAN_TOL
+from tests.test_gpu_parity import check_mixed_median, fixed_hel, fp64_tol, mixed_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,7 +53,7 @@ def test_rewrite_parity_vs_oracle(orc, k, summed, omega, npts, precision):
     bad = np.nonzero(rel > tol)[0]
     assert bad.size == 0, (bad[:5], rel[bad[:5]], tol[bad[:5]])
     if precision == "mixed":
-        assert np.median(rel) <= MIXED_MEDIAN_TOL
+        check_mixed_median(rel, kap)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
