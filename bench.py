@@ -37,17 +37,28 @@ FP32_LANES_PER_SM = 128
 # FP32 148 SMs x 128 lanes x 2 FLOP x 2.032 GHz; FP64 the nominal B300 rate.
 PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 1.25
-# Version of the forward kernel (arithmetic, shared-memory layout, launch
-# shape); bumped with every change to it.  DRAM traffic recorded in
+# Version of the forward kernels (arithmetic, shared-memory layout, launch
+# shape); bumped with every change to them.  DRAM traffic recorded in
 # profiles/traffic.json is reported only for the version it was measured on.
+# FWD: the table-driven kernel (qed_fwd.cu); SPEC: the straight-line
+# specialised kernel (the kernel version its generator writes).
 FWD_KERNEL_VERSION = "fwd-6"
+SPEC_KERNEL_VERSION = "spec-3"
+# Mixed-precision and FP64 per-point bounds against the oracle (as the GPU
+# tests state them): 64 u32 max(kappa, 1) and max(1e-12, 64 u64 kappa).
+U32, U64 = 2.0 ** -24, 2.0 ** -53
+C_MIX = 64
 # The same for the kernel of the distributively rewritten DAG.
 RW_KERNEL_VERSION = "rw-2"
 
 
-def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain"):
-    key = f"{workload}/{prec}" if dag == "plain" else f"{workload}/{dag}/{prec}"
-    version = FWD_KERNEL_VERSION if dag == "plain" else RW_KERNEL_VERSION
+def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain", form: str = "table"):
+    if dag != "plain":
+        key, version = f"{workload}/{dag}/{prec}", RW_KERNEL_VERSION
+    elif form == "specialised":
+        key, version = f"{workload}/specialised/{prec}", SPEC_KERNEL_VERSION
+    else:
+        key, version = f"{workload}/{prec}", FWD_KERNEL_VERSION
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(key)
@@ -121,16 +132,22 @@ class ClockSampler:
 
 def cpu_baseline(mom: np.ndarray, k: int, target_cpu_s: float = 15.0):
     """The oracle, as it stands, on the host cores: batches of the workload's
-    points until about target_cpu_s of CPU time (wall x threads) is spent."""
+    points until about target_cpu_s of CPU time (wall x threads) is spent.
+    Also returns the oracle's |M|^2 and kappa on those points (sample
+    indices cores .. cores + done), against which the GPU results of the same
+    points are compared."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.m2(mom[:cores], threads=cores)  # thread pool start-up
     done, off, t_wall = 0, cores, 0.0
     batch = cores
+    refs, kaps = [], []
     while t_wall * cores < target_cpu_s and off + batch <= len(mom):
         t0 = time.perf_counter()
-        oracle.m2(mom[off:off + batch], threads=cores)
+        r, kp = oracle.m2(mom[off:off + batch], threads=cores, kappa=True)
         dt = time.perf_counter() - t0
+        refs.append(r)
+        kaps.append(kp)
         t_wall += dt
         done += batch
         off += batch
@@ -145,10 +162,36 @@ def cpu_baseline(mom: np.ndarray, k: int, target_cpu_s: float = 15.0):
         t1 += time.perf_counter() - t0
         done1 += b1
         off1 += b1
-    return {"value": done / t_wall, "unit": "points/s", "cores": cores, "kind": "oracle",
+    line = {"value": done / t_wall, "unit": "points/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} of the {len(mom)} k={k} points (all states summed), "
                       f"{t_wall:.1f} s wall on {cores} threads",
             "single_thread_points_per_s": done1 / t1 if t1 > 0 else None}
+    sample = (np.arange(cores, cores + done), np.concatenate(refs), np.concatenate(kaps)) if refs else None
+    return line, sample
+
+
+def error_stats(got, ref, kap, prec):
+    """Relative error of GPU results against the oracle, with the per-point
+    bound of the tests (max_over_bound <= 1: every point within it)."""
+    rel = np.abs(np.asarray(got) / ref - 1.0)
+    if prec == "mixed":
+        bound, text = C_MIX * U32 * np.maximum(kap, 1.0), "64 u32 max(kappa, 1)"
+    else:
+        bound, text = np.maximum(1e-12, 64 * U64 * kap), "max(1e-12, 64 u64 kappa)"
+    return {"n": int(rel.size), "median": float(np.median(rel)), "max": float(rel.max()),
+            "kappa_max": float(np.max(kap)), "max_over_bound": float(np.max(rel / bound)), "bound": text}
+
+
+def measure_peaks(local):
+    """FMA-pipe peaks of this GPU, measured in this run (the roofline
+    denominators), with the SM clocks sampled while they run."""
+    from paper_2511_19456_b300 import measure_fma_peak
+    with ClockSampler(local) as cs:
+        fp32 = measure_fma_peak("mixed")
+        fp64 = measure_fma_peak("fp64")
+    return {"fp32_tflops": fp32, "fp64_tflops": fp64, "clocks": cs.summary(),
+            "how": "independent FMA chains on every SM, CUDA events; FP32 the larger of scalar and "
+                   "packed (two per instruction) chains"}
 
 
 def run_reference(args, workload):
@@ -413,6 +456,174 @@ def run_sweep(args):
     print(json.dumps(res), flush=True)
 
 
+def load_golden(name, per_point):
+    """Rows of a stored oracle file under tests/golden (values the oracle
+    wrote; reading them runs no oracle code)."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return [rows[i:i + per_point] for i in range(0, len(rows), per_point)]
+
+
+def config_legs(peaks, steps):
+    """GPU legs of the four configurations other than the headline one,
+    bounded to about a minute: throughput of both precisions (each plan
+    tuned first), the fraction of the measured FMA peak, the adjoint where
+    the configuration has one, and the GPU results on sample points.  Returns
+    the records and the oracle checks that the cpu_baseline leg runs to fill
+    in each error against the oracle."""
+    import torch
+    from paper_2511_19456_b300 import Batch, Plan, generate
+    recs, checks = {}, []
+
+    def peak(prec):
+        return peaks["fp32_tflops"] if prec == "mixed" else peaks["fp64_tflops"]
+
+    def leg(plan, n, ms, prec):
+        tf = plan.info()["flops_per_point"] * n / (ms * 1e-3) / 1e12
+        return {"n_points": n, "ms": ms, "points_per_s": n / (ms * 1e-3), "tflops": tf,
+                "frac_of_measured_peak": tf / peak(prec)}
+
+    # ---- k = 1, all 16 states, the 65,536 two-body points (FP64 config; mixed beside it)
+    mom = ps.workload_points("compton_k1")
+    d = torch.from_numpy(mom).cuda()
+    out = torch.empty(len(mom), dtype=torch.float64, device="cuda")
+    rec, got = {"config": "e- gamma -> e- gamma, 65,536 flat two-body points, omega = 1, all 16 states"}, {}
+    for prec in ("mixed", "fp64"):
+        plan = Plan(1, precision=prec)
+        tuned = plan.tune(d)
+        ms = time_calls(lambda: plan.eval(d, out), 4 * steps, 3)
+        rec[prec] = dict(leg(plan, len(mom), ms, prec), kernel_form=tuned["form"], block=tuned["block"])
+        got[prec] = out.cpu().numpy().copy()
+    rec["speedup_mixed_vs_fp64"] = rec["fp64"]["ms"] / rec["mixed"]["ms"]
+    recs["compton_k1"] = rec
+    checks.append(("compton_k1", "error_vs_oracle", got, lambda o, m=mom: o.m2(m, kappa=True), "all 65,536 points"))
+
+    # ---- k = 6, one fixed state, 262,144 points: forward and adjoint
+    w = ps.WORKLOADS["compton_k6_fixed"]
+    mom = ps.workload_points("compton_k6_fixed")
+    d = torch.from_numpy(mom).cuda()
+    out = torch.empty(len(mom), dtype=torch.float64, device="cuda")
+    grad = torch.empty((len(mom), 6, 3), dtype=torch.float64, device="cuda")
+    rec, got, gg = {"config": "e- gamma -> e- + 6 gamma, 262,144 RAMBO points, omega = 8, one fixed state "
+                              f"{w['hel']}"}, {}, {}
+    for prec in ("mixed", "fp64"):
+        plan = Plan(6, summed=False, hel=w["hel"], precision=prec)
+        st = steps if prec == "mixed" else 2
+        ms = time_calls(lambda: plan.eval(d, out), st, 1)
+        r = leg(plan, len(mom), ms, prec)
+        got[prec] = out[:256].cpu().numpy().copy()
+        ms_g = time_calls(lambda: plan.eval_grad(d, out, grad), st, 1)
+        r.update(adjoint_ms=ms_g, adjoint_points_per_s=len(mom) / (ms_g * 1e-3), adjoint_over_forward_time=ms_g / ms)
+        _, g32 = plan.eval_grad(d[:32].contiguous())
+        gg[prec] = g32.cpu().numpy()
+        rec[prec] = r
+    rec["speedup_mixed_vs_fp64"] = rec["fp64"]["ms"] / rec["mixed"]["ms"]
+    recs["compton_k6_fixed"] = rec
+    hel = w["hel"]
+    checks.append(("compton_k6_fixed", "error_vs_oracle", got,
+                   lambda o, m=mom[:256]: o.m2(m, sum_mask=0, hel=hel, kappa=True), "the first 256 points"))
+    checks.append(("compton_k6_fixed", "gradient_vs_oracle", gg,
+                   lambda o, m=mom[:32]: o.grad(m, sum_mask=0, hel=hel), "the first 32 points"))
+
+    # ---- the batched stream: 64 seeded requests, k = 1..5, one persistent launch (CUDA graph)
+    reqs = ps.batched_requests()
+    moms = [generate(r["k"], r["n_points"], r["omega"], r["seed"]) for r in reqs]
+    n_tot = sum(r["n_points"] for r in reqs)
+    rec = {"config": f"{len(reqs)} requests, k = 1..5, {n_tot} RAMBO points (generated on the device), "
+                     "omega U[1, 8], all states"}
+    host8 = [ps.points(r["k"], 8, r["omega"], r["seed"]) for r in reqs]
+    got = {}
+    for prec in ("mixed", "fp64"):
+        plans = {k: Plan(k, precision=prec) for k in range(1, 6)}
+        batch = Batch([plans[r["k"]] for r in reqs], [r["n_points"] for r in reqs])
+        outs = batch.outputs()
+        tuned_ms = batch.tune(moms, outs) if prec == "mixed" else None
+        st, wu = (steps, 1) if prec == "mixed" else (1, 0)
+        ms_b = time_calls(lambda: batch.eval(moms, outs), st, wu)
+        seq_outs = [torch.empty_like(o) for o in outs]
+
+        def seq():
+            for r, m, o in zip(reqs, moms, seq_outs):
+                plans[r["k"]].eval(m, o)
+        ms_s = time_calls(seq, st, wu)
+        flops = sum(plans[r["k"]].info()["flops_per_point"] * r["n_points"] for r in reqs)
+        tf = flops / (ms_b * 1e-3) / 1e12
+        rec[prec] = {"batched_ms": ms_b, "batched_points_per_s": n_tot / (ms_b * 1e-3), "tflops": tf,
+                     "frac_of_measured_peak": tf / peak(prec), "sequential_ms": ms_s,
+                     "sequential_points_per_s": n_tot / (ms_s * 1e-3), "launches_batched": 1,
+                     "launches_sequential": len(reqs), "tune_best_ms": tuned_ms, "batch_info": batch.info()}
+        # the first 8 points of every request, host-generated, through the same batched path
+        small = Batch([plans[r["k"]] for r in reqs], [8] * len(reqs))
+        so = small.eval([torch.from_numpy(h).cuda() for h in host8])
+        got[prec] = np.concatenate([o.cpu().numpy() for o in so])
+    rec["speedup_batched_mixed_vs_sequential_fp64"] = rec["fp64"]["sequential_ms"] / rec["mixed"]["batched_ms"]
+    rec["speedup_batched_fp64_vs_sequential_fp64"] = rec["fp64"]["sequential_ms"] / rec["fp64"]["batched_ms"]
+    recs["batched"] = rec
+
+    def batched_oracle(o, hs=host8):
+        parts = [o.m2(h, kappa=True) for h in hs]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
+    checks.append(("batched", "error_vs_oracle", got, batched_oracle, "the first 8 points of each request"))
+
+    # ---- k = 7, all 1024 states: forward and adjoint on slices, errors on the stored oracle points
+    w = ps.WORKLOADS["compton_k7"]
+    n_m, n_d = 16384, 2048
+    mom = ps.points(7, n_m, w["omega"], w["seed"])
+    d = torch.from_numpy(mom).cuda()
+    out = torch.empty(n_m, dtype=torch.float64, device="cuda")
+    grad = torch.empty((n_m, 7, 3), dtype=torch.float64, device="cuda")
+    rec = {"config": f"e- gamma -> e- + 7 gamma, omega = 10, all 1024 states; timed on the first {n_m} (mixed) "
+                     f"and {n_d} (FP64) of the workload's {w['n_points']} points; errors on 512 stored oracle points"}
+    gold = load_golden("k7_summed_oracle.txt", 11)
+    gmom = np.array([[[float(x) for x in row] for row in pt[1:]] for pt in gold]) if gold else None
+    gold_g = load_golden("k7_summed_grad_oracle.txt", 8)
+    for prec in ("mixed", "fp64"):
+        plan = Plan(7, precision=prec)
+        n = n_m if prec == "mixed" else n_d
+        dd, oo, gr = d[:n], out[:n], grad[:n]
+        ms = time_calls(lambda: plan.eval(dd, oo), 2 if prec == "mixed" else 1, 1)
+        r = leg(plan, n, ms, prec)
+        ms_g = time_calls(lambda: plan.eval_grad(dd, oo, gr), 2 if prec == "mixed" else 1, 1)
+        r.update(adjoint_ms=ms_g, adjoint_points_per_s=n / (ms_g * 1e-3), adjoint_over_forward_time=ms_g / ms)
+        if gold:
+            ref = np.array([float(pt[0][0]) for pt in gold])
+            kap = np.array([float(pt[0][1]) for pt in gold])
+            m2 = plan.eval(torch.from_numpy(gmom).cuda()).cpu().numpy()
+            r["error_vs_oracle"] = dict(error_stats(m2, ref, kap, prec), sample="512 stored oracle points")
+        if gold_g:
+            gref = np.array([[[float(x) for x in row] for row in pt[1:]] for pt in gold_g])
+            _, g = plan.eval_grad(torch.from_numpy(np.ascontiguousarray(gmom[:len(gold_g)])).cuda())
+            err = np.abs(g.cpu().numpy() - gref).max(axis=(1, 2)) / np.abs(gref).max(axis=(1, 2))
+            r["gradient_vs_oracle"] = {"n": len(gold_g), "median": float(np.median(err)), "max": float(err.max()),
+                                       "sample": "stored oracle dual-number gradients",
+                                       "measure": "max |g - g_oracle| / max |g_oracle| per point"}
+        rec[prec] = r
+    rec["speedup_mixed_vs_fp64"] = (rec["mixed"]["points_per_s"] / rec["fp64"]["points_per_s"])
+    recs["compton_k7"] = rec
+    return recs, checks
+
+
+def run_oracle_checks(recs, checks):
+    """The oracle side of the configurations' error checks (part of the
+    cpu_baseline leg: the oracle runs on the host cores only here)."""
+    import oracle
+    for cfg, key, got, fn, sample in checks:
+        if key == "gradient_vs_oracle":
+            _, gref = fn(oracle)
+            res = {}
+            for prec, g in got.items():
+                err = np.abs(g - gref).max(axis=(1, 2)) / np.abs(gref).max(axis=(1, 2))
+                res[prec] = {"n": int(err.size), "median": float(np.median(err)), "max": float(err.max()),
+                             "measure": "max |g - g_oracle| / max |g_oracle| per point"}
+        else:
+            ref, kap = fn(oracle)
+            res = {prec: error_stats(g, ref, kap, prec) for prec, g in got.items()}
+        res["sample"] = sample
+        recs[cfg][key] = res
+
+
 def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     import torch
     for _ in range(warmup):
@@ -444,7 +655,11 @@ def main():
                     help="timed steps of the FP64 path (default: --steps)")
     ap.add_argument("--fp64-points", type=int, default=None,
                     help="points of the FP64 legs of the non-headline workloads")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle on the host cores (and with it every error against the oracle)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (k = 1, k = 6 fixed, batched, k = 7)")
+    ap.add_argument("--no-tune", action="store_true", help="time the plans' default kernel form and block")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
@@ -502,9 +717,15 @@ def main():
     legs = [("mixed", args.steps), ("fp64", fp64_steps)]
     if args.only:
         legs = [l for l in legs if l[0] == args.only]
+    # the roofline denominators, measured on this GPU in this run
+    peaks = measure_peaks(local) if not args.only else None
     for prec, steps in legs:
         plan = Plan(k, summed=w["summed"], hel=hel, precision=prec, rewrite=args.dag == "rewrite")
+        # the autotuner (kernel form and block size), on a slice of the
+        # workload, before the timed region
+        tuned = plan.tune(d_mom[:min(n, 1 << 18)]) if not args.only and not args.no_tune else None
         info = plan.info()
+        form = plan.kernel_form
         with ClockSampler(local) as cs:
             ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier)
         launches += steps
@@ -512,13 +733,22 @@ def main():
         pts = n * ws / (ms * 1e-3)
         flops = info["flops_per_point"]
         achieved = flops * n / (ms * 1e-3) / 1e12
-        peak = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        nominal = PEAK_FP32_TFLOPS if prec == "mixed" else PEAK_FP64_TFLOPS
+        if peaks:
+            peak = peaks["fp32_tflops"] if prec == "mixed" else peaks["fp64_tflops"]
+            source = "measured: FMA chains on this GPU in this run (of measured)"
+        else:
+            peak, source = nominal, ("derived from unit counts and the 2032 MHz clock" if prec == "mixed"
+                                     else "nominal B300 FP64 rate")
         res[prec] = {"value": pts, "ms_per_step": ms, "plan": plan, "info": info,
+                     "out": out.cpu().numpy().copy() if not args.only else None,
+                     "kernel": {"form": form, "block": info["block_threads"], "grid": info["grid_blocks"],
+                                "tuned": tuned},
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                                   "unit": "TFLOP/s", "frac": achieved / peak,
-                                  "traffic": recorded_traffic(args.workload, prec, n, args.dag),
-                                  "peak_source": "derived from unit counts and the 2032 MHz clock"
-                                  if prec == "mixed" else "nominal B300 FP64 rate",
+                                  "traffic": recorded_traffic(args.workload, prec, n, args.dag, form),
+                                  "peak_source": source, "peak_nominal": nominal,
+                                  "frac_of_nominal": achieved / nominal,
                                   "pipe": "FP32 FMA" if prec == "mixed" else "FP64 FMA",
                                   "flops_per_point": flops},
                      "clocks": cs.summary()}
@@ -530,15 +760,12 @@ def main():
         r = res[args.only]
         if rank == 0:
             print(json.dumps({"profile_run": args.only, "workload": args.workload, "dag": args.dag,
-                              "n_points": n,
+                              "n_points": n, "kernel": r["kernel"],
                               "ms_per_step": r["ms_per_step"], "value": r["value"],
                               "roofline": r["roofline"]}), flush=True)
         if ws > 1:
             dist.destroy_process_group()
         return
-
-    # measured FMA-chain peaks (context for the derived peaks above)
-    measured = {"fp32_tflops": measure_fma_peak("mixed"), "fp64_tflops": measure_fma_peak("fp64")}
 
     # end to end through the public API on pinned host buffers
     e2e = None
@@ -584,17 +811,29 @@ def main():
                    "l2": f"inputs {n * (k + 3) * 32 / 1e6:.0f} MB per step, larger than the 126 MB L2",
                    "precision": "mixed: FP32 currents and Kahan diagram sums; FP64 momenta, "
                                 "denominators, spin sum"},
+        "kernel": mixed["kernel"],
         "roofline": mixed["roofline"],
         "fp64": {"value": fp64["value"], "unit": "points/s", "ms_per_step": fp64["ms_per_step"],
-                 "steps": fp64_steps, "roofline": fp64["roofline"], "clocks": fp64["clocks"]},
+                 "steps": fp64_steps, "kernel": fp64["kernel"], "roofline": fp64["roofline"],
+                 "clocks": fp64["clocks"]},
         "speedup_mixed_vs_fp64": mixed["value"] / fp64["value"],
-        "peaks_measured_fma_chain": measured,
+        "peaks_measured": peaks,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    checks = []
+    if not args.no_configs:
+        line["configs"], checks = config_legs(peaks, steps=3)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(mom, k)
+        line["cpu_baseline"], sample = cpu_baseline(mom, k)
+        if sample is not None:
+            idx, ref, kap = sample
+            line["error_vs_oracle"] = {
+                "sample": f"the cpu_baseline leg's {len(idx)} points (workload points {idx[0]}..{idx[-1]})",
+                "mixed": error_stats(mixed["out"][idx], ref, kap, "mixed"),
+                "fp64": error_stats(fp64["out"][idx], ref, kap, "fp64")}
+        run_oracle_checks(line.get("configs", {}), checks)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -411,10 +411,12 @@ qed_status qed_debug_inject_alloc_failure(int after);
 const char* qed_status_string(qed_status status);
 
 /* Measured FMA-pipe peak of the current device in TFLOP/s: FP64 for
- * QED_FP64, FP32 for QED_MIXED (independent FMA chains on every SM, CUDA
- * events on `stream`; allocates a small scratch buffer; synchronises).  The
- * |M|^2 kernels are bound by this pipe, so it is their roofline
- * denominator. */
+ * QED_FP64 (about 0.3 s of chains per launch), FP32 for QED_MIXED (the
+ * larger of scalar and packed two-per-instruction FMA chains, the form of
+ * the mixed joins).  Independent chains on every SM, timed with CUDA events
+ * on `stream`; allocates a small scratch buffer; synchronises.  The |M|^2
+ * kernels are bound by this pipe, so it is their roofline denominator.
+ * Not in the paper. */
 qed_status qed_measure_fma_peak(qed_precision precision, double* tflops, void* stream);
 
 /* Linear schedule of the node-reduced DAG, as the kernels execute it: V (+S1)
