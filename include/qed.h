@@ -352,8 +352,10 @@ void qed_batch_destroy(qed_batch_t batch);
  *     caller owns every input and output buffer.
  *   - At most 256 requests; more return QED_EINVAL. Work items are made
  *     larger until they fit the static table (65,536 items).
- *   - The first call on a device looks up the array's device address. Make
- *     that first call before any stream capture on that device.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing). The first call on a
+ *     device may load the library's device code: make it before any stream
+ *     capture on that device.
  *   - Every call shares the array and leaves its contents behind. The
  *     counter is cleared on `stream` before each launch. Calls that overlap
  *     on the GPU, on any stream, race with each other.

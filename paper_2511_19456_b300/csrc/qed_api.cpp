@@ -84,6 +84,10 @@ cudaError_t qed::device_alloc(void** p, size_t bytes) {
 
 qed_status qed::cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return QED_OK;
+  // a failed call that leaves the context usable also leaves its error as
+  // the runtime's last error; clear it, so that the caller's next CUDA call
+  // does not report it (a sticky error stays in the context regardless)
+  cudaGetLastError();
   if (e == cudaErrorMemoryAllocation) return QED_ENOMEM;
   return QED_ECUDA;
 }

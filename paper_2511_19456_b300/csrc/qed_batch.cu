@@ -92,7 +92,11 @@ qed_status configure(qed_batch_s* b) {
   if (e != cudaSuccess) return cuda_status(e);
   if (smem + 64 > (size_t)dev_smem) return QED_EUNSUPPORTED;
   BatchFn fn = batch_fn(b->mixed);
-  e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the limit at the device's maximum, for every batch and for
+  // qed_batch_eval_static alike: none of them lowers it under another's graph
+  int limit = 0;
+  e = max_dynamic_smem((const void*)fn, dev_smem, &limit);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
   int per_sm = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, b->block, smem);

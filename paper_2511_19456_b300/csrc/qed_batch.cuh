@@ -50,4 +50,13 @@ qed_batch_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict
   }
 }
 
+// The largest dynamic shared memory a launch of fn may ask for: the device's
+// opt-in maximum less the kernel's static shared memory.
+inline cudaError_t max_dynamic_smem(const void* fn, int dev_smem, int* out) {
+  cudaFuncAttributes fa{};
+  const cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  *out = dev_smem - (int)fa.sharedSizeBytes;
+  return e;
+}
+
 }  // namespace qed

@@ -11,9 +11,11 @@
 // array until the process exits.
 //
 // In host code the array's name is only a host-side stand-in for the symbol,
-// not a device address. Its address is obtained once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made on
-// that device. Calls share the array, and a call leaves its contents behind.
+// not a device address. Every call obtains its address on the current device
+// with cudaGetSymbolAddress (which allocates nothing), so a device reset,
+// after which the library's device code is loaded anew, is followed as well.
+// The first call on a device may load that code: make it before any stream
+// capture. Calls share the array, and a call leaves its contents behind.
 // The counter is therefore cleared on the stream before every launch, and
 // calls that overlap on the GPU race.
 #include <cuda_runtime.h>
@@ -35,18 +37,11 @@ constexpr size_t kDescOffset = kCounterBytes;
 constexpr size_t kItemsOffset = (kDescOffset + kMaxRequests * sizeof(BatchDesc) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = (kItemsOffset + kMaxItems * sizeof(BatchItem) + 255) / 256 * 256;
 constexpr int kBlock = 128;
-constexpr int kMaxDevices = 128;
 
 // The scratch: counter, request table, work items.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-struct DeviceScratch {
-  bool ready;
-  unsigned char* ptr;   // device address of g_scratch on that device
-};
-
 std::mutex g_lock;                      // guards the host tables below
-DeviceScratch g_dev[kMaxDevices];
 BatchDesc g_desc[kMaxRequests];
 BatchItem g_items[kMaxItems];
 
@@ -70,21 +65,16 @@ extern "C" qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
-  if (dev < 0 || dev >= kMaxDevices) return QED_EUNSUPPORTED;
   auto fn = mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>;
   int dev_smem = 0, sms = 0;
   e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_status(e);
-  if (!g_dev[dev].ready) {
-    // set-up on the first call on this device (that device is current)
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return cuda_status(e);
-    g_dev[dev].ptr = static_cast<unsigned char*>(p);
-    g_dev[dev].ready = true;
-  }
-  unsigned char* base = g_dev[dev].ptr;
+  // the device address of the array on the current device
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return cuda_status(e);
+  unsigned char* base = static_cast<unsigned char*>(p);
   unsigned* d_counter = reinterpret_cast<unsigned*>(base);
   BatchDesc* d_desc = reinterpret_cast<BatchDesc*>(base + kDescOffset);
   BatchItem* d_items = reinterpret_cast<BatchItem*>(base + kItemsOffset);
@@ -118,7 +108,11 @@ extern "C" qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, 
                    [](const BatchItem& x, const BatchItem& y) { return x.k > y.k; });
   for (int r = 0; r < n_req; ++r) g_desc[r].kp = make_params(plans[r], d_momenta[r], n_points[r], d_out[r]);
 
-  e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the kernel's shared-memory limit at the device's maximum, as
+  // qed_batch_create sets it: no call lowers it under a batch's graph
+  int limit = 0;
+  e = max_dynamic_smem((const void*)fn, dev_smem, &limit);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
   int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kBlock, smem);
   if (e != cudaSuccess) return cuda_status(e);

@@ -82,3 +82,70 @@ def test_batch_rejects_bad_requests():
     nn = (ctypes.c_longlong * 1)(-1)
     ph = (ctypes.c_void_p * 1)(a._h.value)
     assert L.qed_batch_create(ph, 1, nn, ctypes.byref(h)) == _lib.QED_EINVAL
+
+
+# ---- the seeded stream of the batched configuration itself
+def oracle_subset(k):
+    """Points of each request compared with the oracle: 4,096 for k <= 4,
+    256 at k = 5 (about 1e8 oracle FLOP per point)."""
+    return 4096 if k <= 4 else 256
+
+
+@pytest.fixture(scope="module")
+def seeded_stream():
+    """The configuration's 64 seeded requests (k = 1..5, 1e3 to 1e6 points,
+    omega in [1, 8]), every point from the host generator."""
+    reqs = ps.batched_requests()
+    return reqs, [ps.points(r["k"], r["n_points"], r["omega"], r["seed"]) for r in reqs]
+
+
+@pytest.fixture(scope="module")
+def seeded_stream_oracle(orc, seeded_stream):
+    reqs, moms = seeded_stream
+    return [orc.m2(m[:oracle_subset(r["k"])], kappa=True) for r, m in zip(reqs, moms)]
+
+
+def _static_call(plans, n, moms, outs):
+    L = _lib.lib()
+    nreq = len(plans)
+    ph = (ctypes.c_void_p * nreq)(*[p._h.value for p in plans])
+    nn = (ctypes.c_longlong * nreq)(*n)
+    pm = (ctypes.c_void_p * nreq)(*[m.data_ptr() for m in moms])
+    po = (ctypes.c_void_p * nreq)(*[o.data_ptr() for o in outs])
+    return L.qed_batch_eval_static(ph, nreq, nn, pm, po, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+@pytest.mark.parametrize("entry", ["qed_batch_eval", "qed_batch_eval_static"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_seeded_batched_stream_vs_oracle(seeded_stream, seeded_stream_oracle, entry, precision):
+    """All 64 requests (10.9 M points) in one persistent launch, then each
+    request's first points against the oracle at the per-point bounds."""
+    from tests.test_gpu_parity import check_mixed_median
+    reqs, moms = seeded_stream
+    plans = {k: Plan(k, precision=precision) for k in range(1, 6)}
+    req_plans = [plans[r["k"]] for r in reqs]
+    n = [r["n_points"] for r in reqs]
+    d = [torch.from_numpy(m).cuda() for m in moms]
+    if entry == "qed_batch_eval":
+        batch = Batch(req_plans, n)
+        if precision == "mixed":
+            batch.tune(d, batch.outputs())
+        outs = batch.eval(d)
+    else:
+        outs = [torch.full((c,), -1.0, dtype=torch.float64, device="cuda") for c in n]
+        assert _static_call(req_plans, n, d, outs) == _lib.QED_OK
+    torch.cuda.synchronize()
+    rels, kaps = [], []
+    for r, o, (ref, kap) in zip(reqs, outs, seeded_stream_oracle):
+        got = o[:len(ref)].cpu().numpy()
+        rel = np.abs(got / ref - 1.0)
+        tol = np.maximum(1e-12, 64 * 2.0 ** -53 * kap) if precision == "fp64" else mixed_tol(r["k"], kap)
+        assert np.all(rel <= tol), (r, float(rel.max()))
+        assert torch.isfinite(o).all() and (o > 0).all()
+        rels.append(rel)
+        kaps.append(kap)
+    rel, kap = np.concatenate(rels), np.concatenate(kaps)
+    print(f"\n{entry} {precision}: {rel.size} oracle points over {len(reqs)} requests, "
+          f"median rel {np.median(rel):.3e} max {rel.max():.3e} (kappa max {kap.max():.1f})")
+    if precision == "mixed":
+        check_mixed_median(rel, kap)
