@@ -91,9 +91,10 @@ __device__ __forceinline__ void ld3(const double* e, double ev[3]) {
 // ------------------------------------------------------------ set-up
 // Per point, FP32-mixed (a1-a3 for a team of one lane per photon subset,
 // TEAM = 2^n, k <= 4): the momenta, the propagator entries of every subset
-// and the external states, with as few FP64 instructions as the method
-// allows (each occupies B300's FP64 pipe for a warp's worth of lanes; this
-// set-up needs about 15 per point where the direct form needs about 45).
+// and the external states, with few FP64 instructions (on B300 each warp
+// instruction holds the FP64 pipe for many cycles; ncu counts 16 FP64
+// arithmetic instructions per point here against 26 for the direct form,
+// whose per-photon adds also issue for lanes without the photon).
 //   1. each lane loads one FP64 momentum component and splits it into a
 //      float-float pair (hi + lo, exact to about 2^-48);
 //   2. the Lorentz invariants, one Minkowski product per lane in FP64:
