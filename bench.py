@@ -417,7 +417,7 @@ def run_abc(args):
 
 
 def run_sweep(args):
-    """Node-reduction sweep (paper Sec. III-E, Fig. f_optimization): the CDAG
+    """Node-reduction sweep (paper Sec. III-D, Fig. f_optimization): the CDAG
     of e- gamma -> e- + 4 gamma, one fixed spin state, FP64, executed node by
     node after 0, 10, ..., all 140 single node reductions.  For each state:
     nodes, FLOPs per point, points/s, the measured speed-up over the

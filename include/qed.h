@@ -4,7 +4,7 @@
  * Process: e-(p) gamma(k0) -> e-(p') + gamma(k1) ... gamma(kK), tree level,
  * K = k outgoing photons, n = k + 1 photons on the electron line and (k+1)!
  * Feynman diagrams (paper Sec. III-A).  The amplitude of one diagram follows
- * the QED Feynman rules of paper Sec. I-B (Eq. 1 is the k = 1 case):
+ * the QED Feynman rules of paper Sec. I-D (Eq. 1 is the k = 1 case):
  *
  *   A_sigma = ubar(p') eps/_{sigma(n)} S(Q_{n-1}) ... S(Q_1) eps/_{sigma(1)} u(p),
  *   S(Q) = (Q/ + m) / (Q^2 - m^2),  Q_i = p + sum_{l<=i} c_l k_{sigma(l)},
@@ -108,7 +108,7 @@ typedef struct {
 /* Forward kernel forms of a plan.  The DAG builder either linearises the
  * DAG into instruction tables or emits a straight-line specialised kernel
  * at build time (the paper's framework generates straight-line code from
- * the scheduled DAG, Sec. II-A; Sec. III-E measures full inlining).
+ * the scheduled DAG, Sec. II-A; Sec. III-D measures full inlining).
  *   QED_KERNEL_TABLE: one kernel per (k, spin mode, precision) that reads the
  *     plan's linear schedule (instruction, phase and photon-set tables) from
  *     device memory at run time.  Every plan has it.
@@ -189,7 +189,7 @@ typedef struct {
 qed_status qed_abc_plan_create(const qed_abc_process* process, qed_precision precision, int rewrite,
                                qed_plan_t* out);
 
-/* The node-reduction sweep (paper Sec. III-E, Fig. f_optimization).
+/* The node-reduction sweep (paper Sec. III-D, Fig. f_optimization).
  *
  * qed_reduction_steps: the number of single node reductions that take the
  * per-diagram CDAG of e- gamma -> e- + k gamma (k in 1..6, one spin state)
@@ -224,6 +224,11 @@ qed_status qed_tape_export(int k, int steps, qed_tape_desc_t* desc, void* instr,
 qed_status qed_tape_plan_create(const qed_process* process, const qed_spin_cfg* spin, int reduction_steps,
                                 qed_plan_t* out);
 
+/* Sizes and counted arithmetic of a plan: the per-diagram and node-reduced
+ * DAG sizes of Table I (Sec. III-A), (k+1)! diagrams, the spin states, the
+ * FLOPs per point, and the kernel in use.  The paper prints the sizes; the
+ * counting convention (add/sub/mul 1, fma 2) is this library's.
+ * QED_EINVAL for NULL arguments. */
 qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 
 /* Selects the forward kernel form (qed_kernel_form) that qed_eval,
@@ -248,13 +253,18 @@ qed_status qed_plan_set_kernel_form(qed_plan_t plan, int form);
 qed_status qed_plan_tune(qed_plan_t plan, const double* d_momenta, long long n, double* d_out_m2, void* stream,
                          int* form, int* block, double* best_ms);
 
-/* out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4
+/* The evaluation of the computable DAG (Sec. II-B: it takes the
+ * four-momenta of all particles and returns one real value; tasks U, V, S1,
+ * S2 and Sum, the Feynman rules of Sec. I-D) at N phase-space points:
+ * out_m2[i] = |M|^2 at point i.  d_momenta: device pointer to N*(k+3)*4
  * doubles, 8-byte aligned; d_out_m2: device pointer to N doubles; stream: a
- * cudaStream_t (NULL = legacy default stream).  Asynchronous. */
+ * cudaStream_t (NULL = legacy default stream).  Asynchronous.  QED_EINVAL for
+ * a NULL or misaligned buffer or N < 0. */
 qed_status qed_eval(qed_plan_t plan, const double* d_momenta, long long n,
                     double* d_out_m2, void* stream);
 
-/* As qed_eval, plus d_grad[N][k][3] = d|M|^2 / d(px, py, pz) of the k
+/* Not in the paper (the adjoint of its DAG): as qed_eval, plus
+ * d_grad[N][k][3] = d|M|^2 / d(px, py, pz) of the k
  * outgoing photons (slots 3..k+2), their energies on shell, E_j = |k_j|, and
  * every other momentum held fixed.  d_out_m2 may be NULL.  Reverse mode
  * through the same reduced DAG, sub-currents recomputed per photon set;
@@ -292,7 +302,7 @@ qed_status qed_grad_workspace_bytes(qed_plan_t plan, long long* bytes);
 qed_status qed_eval_grad_ws(qed_plan_t plan, const double* d_momenta, long long n, double* d_out_m2,
                             double* d_grad, void* d_workspace, long long workspace_bytes, void* stream);
 
-/* End-to-end form of qed_eval on HOST buffers: copies the momenta to the
+/* Not in the paper.  End-to-end form of qed_eval on HOST buffers: copies the momenta to the
  * device, evaluates and copies |M|^2 back, chunked so that copies overlap
  * the kernels.  Uses device staging owned by the plan, grown (allocated) on
  * the first call that needs more; synchronises `stream` before returning.
@@ -302,9 +312,11 @@ qed_status qed_eval_grad_ws(qed_plan_t plan, const double* d_momenta, long long 
 qed_status qed_eval_host(qed_plan_t plan, const double* h_momenta, long long n,
                          double* h_out_m2, void* stream);
 
+/* Frees a plan and everything it owns (NULL: no-op). */
 void qed_plan_destroy(qed_plan_t plan);
 
-/* Batched evaluation of n_req requests of different k in ONE persistent
+/* Not in the paper.
+ * Batched evaluation of n_req requests of different k in ONE persistent
  * launch (spin-summed plans, k <= 5, all of the same precision).  The host
  * cuts request r's n_points[r] points into work items of about equal
  * arithmetic, most expensive k first; persistent CTAs take items from a
@@ -317,21 +329,22 @@ void qed_plan_destroy(qed_plan_t plan);
 qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long* n_points,
                             qed_batch_t* out);
 
-/* Evaluates every request: d_momenta[r] -> d_out[r] (device pointers, sizes
+/* Not in the paper.  Evaluates every request: d_momenta[r] -> d_out[r] (device pointers, sizes
  * as given at creation).  Copies the request table (pointers) and replays the
  * graph on `stream`; asynchronous. */
 qed_status qed_batch_eval(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
                           void* stream);
 
-/* Autotuner: times block sizes {64, 128, 256} x item sizes {1e8 .. 6.4e9
+/* Not in the paper.  Autotuner: times block sizes {64, 128, 256} x item sizes {1e8 .. 6.4e9
  * FLOPs} on the given buffers, keeps the fastest, rebuilds the graph and
  * returns its time per evaluation in *best_ms (may be NULL).  Synchronous. */
 qed_status qed_batch_tune(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
                           void* stream, double* best_ms);
 
-/* Current launch shape of a batch. */
+/* Not in the paper.  Current launch shape of a batch. */
 qed_status qed_batch_info(qed_batch_t batch, int* block, double* work_target, long long* n_items);
 
+/* Frees a batch (not its plans; NULL: no-op). */
 void qed_batch_destroy(qed_batch_t batch);
 
 /* Allocation-free batched evaluation.  The paper has no counterpart; this
@@ -367,7 +380,7 @@ qed_status qed_dag_counts(int k, qed_dag_counts_t* out);
 
 /* Device-side phase-space points, the step before the |M|^2 path of a Monte
  * Carlo event generator (the paper motivates the method by Monte Carlo
- * sampling, Sec. III-E).  Writes points offset .. offset+n-1 of the seeded
+ * sampling, Sec. I-C and III-E).  Writes points offset .. offset+n-1 of the seeded
  * stream into d_momenta[n][k+3][4] (layout as above), with the same recipe
  * and counter-based SplitMix64 draws as the host generator:
  *   - k = 1: flat two-body, uniform in the CM solid angle;
@@ -410,6 +423,7 @@ qed_status qed_cross_section(qed_plan_t plan, double omega, unsigned long long s
  * QED_EINVAL if after < -1. The paper has no counterpart. */
 qed_status qed_debug_inject_alloc_failure(int after);
 
+/* A static English description of a status code. */
 const char* qed_status_string(qed_status status);
 
 /* Measured FMA-pipe peak of the current device in TFLOP/s: FP64 for
@@ -421,7 +435,9 @@ const char* qed_status_string(qed_status status);
  * Not in the paper. */
 qed_status qed_measure_fma_peak(qed_precision precision, double* tflops, void* stream);
 
-/* Linear schedule of the node-reduced DAG, as the kernels execute it: V (+S1)
+/* The static schedule of Sec. II-A (the scheduler's topological order,
+ * here grouped into phases and photon sets): the linear schedule of the
+ * node-reduced DAG, as the kernels execute it: V (+S1)
  * instructions (16 bytes each), phases (24 bytes) and photon-set entries (16
  * bytes); layouts in csrc/dag.hpp.  Host only, no GPU needed.  Call with NULL
  * buffers to get the sizes in *desc, then with buffers of those sizes. */

@@ -5,7 +5,7 @@
 // call this file: only the tests, the smoke check and the benchmark's CPU
 // baseline leg use it.  It shares no code with the CUDA path.
 //
-// What it computes (paper Sec. I-B, Feynman rules and Eq. 1; Sec. III-A for
+// What it computes (paper Sec. I-D, Feynman rules and Eq. 1; Sec. III-A for
 // the (n+1)! diagram count):
 //
 //   |M|^2 = sum_{lambda} | sum_{sigma in S_n} A_sigma(lambda) |^2 ,

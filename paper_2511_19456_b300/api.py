@@ -216,7 +216,7 @@ class AbcPlan(Plan):
 class TapePlan(Plan):
     """Node-by-node execution of the CDAG of e- gamma -> e- + k gamma (one
     fixed spin state, k <= 5, FP64) after `reduction_steps` single node
-    reductions: the node-reduction sweep of the paper's Sec. III-E."""
+    reductions: the node-reduction sweep of the paper's Sec. III-D."""
 
     def __init__(self, k: int, hel, reduction_steps: int, mass: float = 1.0, charge: float = 1.0):
         if hel is None or len(hel) != k + 3:

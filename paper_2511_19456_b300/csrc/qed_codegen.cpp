@@ -2,7 +2,7 @@
 //
 // The paper's framework compiles the scheduled CDAG into one function of
 // straight-line code, every task inlined (Sec. II-A, the code generation
-// step; Sec. III-E measures full inlining against calls).  This program does
+// step; Sec. III-D measures full inlining against calls).  This program does
 // the same for the spin-summed plans of k = 1..4: it builds the node-reduced
 // DAG and its linear schedule (dag.cpp: generate, reduce, build_schedule) and
 // writes one CUDA kernel per k and precision in which every instruction of the

@@ -1,5 +1,5 @@
 // Node-by-node execution of a CDAG in any node-reduction state (the
-// node-reduction sweep of Sec. III-E, Fig. f_optimization).
+// node-reduction sweep of Sec. III-D, Fig. f_optimization).
 //
 // The tape holds every compute node of the DAG, grouped by level (longest
 // path from the external states).  A team of 32 threads evaluates one point:

@@ -1,6 +1,6 @@
 """Pins of the FP64 oracle against what the paper and the mathematics fix.
 
-The oracle is a brute-force sum over every Feynman diagram (paper Sec. I-B,
+The oracle is a brute-force sum over every Feynman diagram (paper Sec. I-D,
 Eq. 1 and the Feynman rules there; Sec. III-A for the (n+1)! diagrams).  It is
 pinned here by facts that do not come from the oracle itself:
 
