@@ -112,11 +112,16 @@ typedef struct {
  *   QED_KERNEL_TABLE: one kernel per (k, spin mode, precision) that reads the
  *     plan's linear schedule (instruction, phase and photon-set tables) from
  *     device memory at run time.  Every plan has it.
- *   QED_KERNEL_SPECIALISED: a kernel generated from the same schedule when
- *     the library is built (csrc/qed_codegen.cpp), with every instruction
- *     expanded into straight-line code whose photon, polarisation, source,
- *     destination and propagator are literals.  Spin-summed plans of the
- *     node-reduced DAG with k <= 4.
+ *   QED_KERNEL_SPECIALISED: a kernel shaped for the plan's kind.
+ *     Spin-summed plans of the node-reduced DAG with k <= 4: generated from
+ *     the same schedule when the library is built (csrc/qed_codegen.cpp),
+ *     with every instruction expanded into straight-line code whose
+ *     photon, polarisation, source, destination and propagator are
+ *     literals.  One fixed state in mixed precision, k <= 6: the
+ *     register-join kernel (csrc/qed_fix.cu) on the schedule that keeps
+ *     every level below the leaves; per photon set each lane of one warp
+ *     builds one leaf, keeps a left leaf in registers and joins it with
+ *     every right leaf of the set, from per-lane items of two ints.
  * Both compute the same DAG; their results agree to rounding. */
 typedef enum { QED_KERNEL_TABLE = 0, QED_KERNEL_SPECIALISED = 1 } qed_kernel_form;
 

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqedm2.so")
 GEN = os.path.join(BUILD, "qed_spec_gen.cu")
 SOURCES = ["dag.cpp", "qed_api.cpp", "qed_fwd.cu", "qed_rw.cu", "abc_kernel.cu", "qed_tape.cu", "qed_adj.cu",
-           "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu"]
+           "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu", "qed_fix.cu"]
 HEADERS = ["dag.hpp", "qed_types.h", "qed_device.cuh", "qed_team.cuh", "qed_eval.cuh", "qed_plan.hpp", "qed_batch.cuh",
            "qed_spec.cuh"]
 GENERATOR = ["qed_codegen.cpp", "dag.cpp", "dag.hpp", "qed_types.h"]

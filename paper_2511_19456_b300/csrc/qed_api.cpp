@@ -53,6 +53,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_lane_tab);
   cudaFree(p->d_dep_tab);
   cudaFree(p->d_part_tab);
+  cudaFree(p->d_fix_items);
   cudaFree(p->d_stage);
   if (p->ev_scratch) cudaEventDestroy(p->ev_scratch);
   for (int i = 0; i < 2; ++i) {
@@ -127,6 +128,12 @@ KParams qed::make_params(const qed_plan_s* P, const double* mom, long long n, do
   kp.fixed_sout = P->fixed_sout;
   kp.fixed_pol_bits = 0;
   for (int j = 0; j < 8; ++j) kp.fixed_pol_bits |= (unsigned)(P->fixed_pol[j] & 1) << j;
+  kp.fix_items = P->d_fix_items;
+  kp.fix_ngroups = P->fix_ngroups;
+  for (int g = 0; g < 9; ++g) kp.fix_group[g] = P->fix_group[g];
+  kp.fix_set_off = P->fix_set_off;
+  kp.fix_rbase = P->fix_rbase;
+  kp.fix_ncur = P->fix_ncur;
   if (P->is_tape) {
     kp.tape = P->d_tape;
     kp.tape_levels = P->d_levels;
@@ -298,6 +305,101 @@ cudaError_t configure_form(qed_plan_s::Form* f, int sms) {
   f->ok = e == cudaSuccess && per_sm >= 1;
   f->grid = per_sm * sms;
   return e;
+}
+
+// One fixed state, FP32-mixed: the register-join form (qed_fix.cu), on the
+// schedule that keeps every level below the leaves.  Items are two ints:
+//   source current | destination current << 16 (0xffff: kept in registers),
+//   polarisation vector | propagator photon set << 8 | side << 24,
+// with the fixed spinors u and ubar as currents 0 and 1 and the schedule's
+// stored currents from 2.  The kept levels come first, one group per phase;
+// then, per photon set, one item per lane of a warp (part): the NL left
+// leaves (kept in the lanes' registers), the NR right leaves (destination:
+// the position in the warp's current buffer of the set's right leaves), and
+// idle lanes (no store, no join); then one set of idle items per warp (a
+// software-pipelined kernel forms its next set's items while it joins the
+// current one).  Two alternating buffers per warp of a team.  Items without
+// a propagator name photon set 0 (the kernel's identity entry).  Leaves the
+// plan without the form where the kernel or the schedule's shape does not
+// allow it.
+qed_status setup_fixed_join(qed_plan_s* P, int dev_smem, int sms) {
+  const KernelChoice kc = fixed_join_kernel(P->k);
+  if (!kc.fn) return QED_OK;
+  const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
+  const int team = kc.team;
+  Schedule sc;
+  try {
+    sc = build_schedule(k, false, h - 1, r - 1);
+  } catch (const std::bad_alloc&) {
+    return QED_ENOMEM;
+  } catch (...) {
+    return QED_EUNSUPPORTED;
+  }
+  const int NL = sc.n_left_leaves, NR = sc.n_right_leaves;
+  const int wl = std::min(team, 32), nw = team / wl;   // lanes per warp (part), warps per team
+  if (sc.n_set_phases != 1 || NL + NR > wl || sc.n_stored_phases > 8) return QED_OK;
+  const int rbase = 2 + sc.stored_currents, ncur = rbase + nw * 2 * NR;
+  if (ncur >= 0xffff) return QED_OK;
+  std::vector<uint32_t> w;
+  auto push = [&](const Instr& in, int dst) {
+    const uint32_t src = in.src < 0 ? (uint32_t)in.side : (uint32_t)in.src + 2;
+    const uint32_t eps = (uint32_t)in.photon * 2 + (uint32_t)(P->fixed_pol[in.photon] & 1);
+    w.push_back(src | ((uint32_t)dst << 16));
+    w.push_back(eps | ((uint32_t)in.post << 8) | ((uint32_t)in.side << 24));
+  };
+  int group[9] = {0};
+  for (int g = 0; g < sc.n_stored_phases; ++g) {
+    const Phase& ph = sc.phases[g];
+    for (int slot = 0; slot < 2; ++slot)
+      for (int i = 0; i < ph.cnt[slot]; ++i) {
+        const Instr& in = sc.instr[ph.beg[slot] + i];
+        push(in, in.dst + 2);
+      }
+    group[g + 1] = (int)(w.size() / 2);
+  }
+  const int set_off = (int)(w.size() / 2);
+  for (size_t s = 0; s < sc.sets.size(); ++s) {
+    const Phase& ph = sc.phases[sc.sets[s].phase0];
+    if (ph.cnt[0] != NL || ph.cnt[1] != NR || ph.level[0] != h || ph.level[1] != r) return QED_OK;
+    for (int lane = 0; lane < wl; ++lane) {
+      if (lane < NL) {
+        const Instr& in = sc.instr[ph.beg[0] + lane];
+        if (in.post != 0 || in.side != 0) return QED_OK;
+        push(in, 0xffff);
+      } else if (lane < NL + NR) {
+        const Instr& in = sc.instr[ph.beg[1] + lane - NL];
+        if (in.side != 1) return QED_OK;
+        push(in, lane - NL);
+      } else {
+        w.push_back(0xffffu << 16);
+        w.push_back(0);
+      }
+    }
+  }
+  for (int lane = 0; lane < nw * wl; ++lane) {   // idle sets after the last, one per warp
+    w.push_back(0xffffu << 16);
+    w.push_back(0);
+  }
+  const int bytes = team_layout(k, 4, ncur).bytes;
+  qed_plan_s::Form f{kc, 128, 0, 0, false, bytes};
+  f.smem = (size_t)(f.block / team) * bytes;
+  while (f.smem > (size_t)dev_smem && f.block > team) {
+    f.block /= 2;
+    f.smem = (size_t)(f.block / team) * bytes;
+  }
+  if (f.smem > (size_t)dev_smem) return QED_OK;
+  std::vector<int> items(w.begin(), w.end());
+  cudaError_t e = upload(&P->d_fix_items, items);
+  if (e == cudaSuccess) e = configure_form(&f, sms);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!f.ok) return QED_OK;
+  P->fix_ngroups = sc.n_stored_phases;
+  for (int g = 0; g < 9; ++g) P->fix_group[g] = group[g];
+  P->fix_set_off = set_off;
+  P->fix_rbase = rbase;
+  P->fix_ncur = ncur;
+  P->forms[1] = f;
+  return QED_OK;
 }
 
 // The form a new plan starts with, from measurements on B300: the
@@ -501,6 +603,10 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
         P->forms[1] = f;
       }
     }
+  }
+  if (!rewrite && !P->summed && mixed) {
+    qed_status fs = setup_fixed_join(P, dev_smem, sms);
+    if (fs != QED_OK) { free_plan(P); return fs; }
   }
   P->form.store(default_form(P));
   if (!rewrite) {
@@ -744,10 +850,10 @@ qed_status qed_plan_info(qed_plan_t P, qed_plan_info_t* info) {
     info->flops_literal_s2_per_point = P->tp.flops;
     info->reduction_steps = P->tp.steps;
   }
-  info->team_threads = P->kc.team;
-  info->smem_bytes_per_team = P->forms[P->form.load()].team_bytes;
-  info->precision = (int)P->prec;
   const int f = P->form.load();
+  info->team_threads = P->forms[f].kc.team;
+  info->smem_bytes_per_team = P->forms[f].team_bytes;
+  info->precision = (int)P->prec;
   info->kernel_form = f;
   info->kernel_forms = (P->forms[0].ok ? 1 : 0) | (P->forms[1].ok ? 2 : 0);
   info->block_threads = P->forms[f].block;

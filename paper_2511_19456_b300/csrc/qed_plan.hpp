@@ -31,6 +31,9 @@ struct SpecKernel {
   int team, ncur, team_bytes;
 };
 SpecKernel spec_forward_kernel(int k, bool mixed);
+// One fixed state, FP32-mixed, register-join form (qed_fix.cu), k = 1..6;
+// fn == nullptr otherwise.
+KernelChoice fixed_join_kernel(int k);
 const char* spec_version();
 }  // namespace qed
 
@@ -99,6 +102,9 @@ struct qed_plan_s {
   uint16_t* d_lane_tab = nullptr;   // spin-summed plans: leaf variants per (set, lane)
   uint16_t* d_dep_tab = nullptr;    // spin-summed plans: polarisation patterns per (set, leaf variant)
   uint16_t* d_part_tab = nullptr;   // mixed adjoint: propagator of each partial-sum slot per set
+  // one fixed state, mixed: the register-join form's items (KParams::fix_*)
+  int* d_fix_items = nullptr;
+  int fix_ngroups = 0, fix_group[9] = {0}, fix_set_off = 0, fix_rbase = 0, fix_ncur = 0;
   int n_part = 0;
   int device = 0;
   // staging for qed_eval_host (one call at a time per plan: stage_lock)

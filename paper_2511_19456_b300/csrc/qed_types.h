@@ -147,6 +147,19 @@ struct KParams {
   // names its slot as pad - 1 (pad = 0: no slot, direct FP64 accumulation)
   const uint16_t* part_tab;
   int n_part;
+  // one fixed state, register-join form (qed_fix.cu): fix_items holds the
+  // items (two ints each, 8-byte aligned) of the kept levels, in groups of
+  // independent items
+  // [fix_group[g], fix_group[g+1]), then one item per lane of a warp (part)
+  // per photon set from fix_set_off; the right leaves of a set go to one of
+  // its warp's two alternating buffers of NR currents (the warps' buffers
+  // follow each other from current fix_rbase); fix_ncur currents per team
+  const int* fix_items;
+  int fix_ngroups;
+  int fix_group[9];
+  int fix_set_off;
+  int fix_rbase;
+  int fix_ncur;
   // tape plans (node-reduction sweep)
   const TapeInstr* tape;
   const int* tape_levels;          // instruction range of each level

@@ -116,9 +116,11 @@ def test_tune_picks_a_form_and_stays_correct(orc, k, precision):
     assert np.all(np.abs(got / ref - 1.0) <= tol(precision, k, kap))
 
 
-def test_only_summed_plain_plans_have_the_specialised_form():
+def test_which_plans_have_the_specialised_form():
+    # one fixed state: only the mixed form has one (the register-join kernel)
     fixed = Plan(3, summed=False, hel=[1, 2, -1, 1, 2, 1])
     assert fixed.kernel_forms() == ["table"]
+    assert Plan(3, summed=False, hel=[1, 2, -1, 1, 2, 1], precision="mixed").kernel_forms() == ["table", "specialised"]
     with pytest.raises(QedError) as ei:
         fixed.set_kernel_form("specialised")
     assert ei.value.status == QED_EUNSUPPORTED
