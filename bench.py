@@ -624,10 +624,18 @@ def run_oracle_checks(recs, checks):
         recs[cfg][key] = res
 
 
-def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
+def time_device(plan, d_mom, out, steps, warmup, stream, barrier, grad=None):
+    """Device time per call of qed_eval (or, with a gradient buffer, of
+    qed_eval_grad) with CUDA events on the launching stream."""
     import torch
+
+    def call():
+        if grad is None:
+            plan.eval(d_mom, out, stream=stream)
+        else:
+            plan.eval_grad(d_mom, out, grad, stream=stream)
     for _ in range(warmup):
-        plan.eval(d_mom, out, stream=stream)
+        call()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -635,7 +643,7 @@ def time_device(plan, d_mom, out, steps, warmup, stream, barrier):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        plan.eval(d_mom, out, stream=stream)
+        call()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -663,6 +671,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="time one precision only (profiling runs)")
+    ap.add_argument("--grad", action="store_true",
+                    help="profiling runs (--only): time qed_eval_grad (|M|^2 and the adjoint) instead of qed_eval")
     ap.add_argument("--n-points", type=int, default=None,
                     help="override the workload's point count (profiling runs)")
     ap.add_argument("--dag", choices=["plain", "rewrite"], default="plain",
@@ -726,8 +736,9 @@ def main():
         tuned = plan.tune(d_mom[:min(n, 1 << 18)]) if not args.only and not args.no_tune else None
         info = plan.info()
         form = plan.kernel_form
+        g_buf = torch.empty((n, k, 3), dtype=torch.float64, device="cuda") if args.grad and args.only else None
         with ClockSampler(local) as cs:
-            ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier)
+            ms = time_device(plan, d_mom, out, steps, args.warmup, stream, barrier, grad=g_buf)
         launches += steps
         ms = max_over_ranks(ms, device="cuda")
         pts = n * ws / (ms * 1e-3)
@@ -759,7 +770,7 @@ def main():
         # profiling run: one precision, no end-to-end leg, a short line
         r = res[args.only]
         if rank == 0:
-            print(json.dumps({"profile_run": args.only, "workload": args.workload, "dag": args.dag,
+            print(json.dumps({"profile_run": args.only, "grad": args.grad, "workload": args.workload, "dag": args.dag,
                               "n_points": n, "kernel": r["kernel"],
                               "ms_per_step": r["ms_per_step"], "value": r["value"],
                               "roofline": r["roofline"]}), flush=True)

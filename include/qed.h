@@ -326,9 +326,13 @@ void qed_plan_destroy(qed_plan_t plan);
  * cuts request r's n_points[r] points into work items of about equal
  * arithmetic, most expensive k first; persistent CTAs take items from a
  * device counter, which never makes one CTA wait for another.  The counter
- * reset and the launch are captured once in a CUDA graph.  The batch keeps
- * the plans (they must outlive it), allocates its item list, request table
- * and counter, and is not safe for concurrent use from two streams.
+ * reset and the launch are captured once in a CUDA graph.  Kernel forms as
+ * for a plan (qed_kernel_form): QED_KERNEL_TABLE runs the table-driven point
+ * evaluation of every k, QED_KERNEL_SPECIALISED (a new batch's form) the
+ * straight-line specialised one for k <= 4 and the table-driven one for
+ * k = 5.  The batch keeps the plans (they must outlive it), allocates its
+ * item list, request table and counter, and is not safe for concurrent use
+ * from two streams.
  * Errors: QED_EINVAL (NULL, n < 0, mixed precisions), QED_EUNSUPPORTED
  * (fixed spin, k > 5), QED_ENOMEM, QED_ECUDA. */
 qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long* n_points,
@@ -340,14 +344,24 @@ qed_status qed_batch_create(const qed_plan_t* plans, int n_req, const long long*
 qed_status qed_batch_eval(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
                           void* stream);
 
-/* Not in the paper.  Autotuner: times block sizes {64, 128, 256} x item sizes {1e8 .. 6.4e9
- * FLOPs} on the given buffers, keeps the fastest, rebuilds the graph and
- * returns its time per evaluation in *best_ms (may be NULL).  Synchronous. */
+/* Not in the paper.  Autotuner: times kernel forms {table, specialised} x block sizes
+ * {64, 128, 256} x item sizes {1e8, 4e8, 1.6e9 FLOPs} on the given buffers,
+ * keeps the fastest, rebuilds the graph and returns its time per evaluation
+ * in *best_ms (may be NULL).  Synchronous. */
 qed_status qed_batch_tune(qed_batch_t batch, const double* const* d_momenta, double* const* d_out,
                           void* stream, double* best_ms);
 
 /* Not in the paper.  Current launch shape of a batch. */
 qed_status qed_batch_info(qed_batch_t batch, int* block, double* work_target, long long* n_items);
+
+/* Not in the paper.  Selects the batch's kernel form (qed_kernel_form) and
+ * rebuilds its graph; synchronous.  Errors: QED_EINVAL (NULL batch,
+ * unknown form), QED_EUNSUPPORTED / QED_ECUDA from the rebuild (the old form
+ * is kept). */
+qed_status qed_batch_set_kernel_form(qed_batch_t batch, int form);
+
+/* Not in the paper.  The batch's kernel form in *form.  QED_EINVAL for NULL. */
+qed_status qed_batch_kernel_form(qed_batch_t batch, int* form);
 
 /* Frees a batch (not its plans; NULL: no-op). */
 void qed_batch_destroy(qed_batch_t batch);

@@ -107,6 +107,8 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_double)]),
     ("qed_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(_ll)]),
+    ("qed_batch_set_kernel_form", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("qed_batch_kernel_form", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     ("qed_batch_destroy", None, [_vp]),
     ("qed_batch_eval_static", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_ll),
                                              ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),

@@ -368,10 +368,16 @@ class Batch:
         return ms.value
 
     def info(self) -> dict:
-        b, t, n = ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
+        b, t, n, f = ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong(), ctypes.c_int()
         check(_lib.lib().qed_batch_info(self._h, ctypes.byref(b), ctypes.byref(t), ctypes.byref(n)),
               "qed_batch_info")
-        return {"block": b.value, "work_target_flops": t.value, "n_items": n.value}
+        check(_lib.lib().qed_batch_kernel_form(self._h, ctypes.byref(f)), "qed_batch_kernel_form")
+        form = next(name for name, v in Plan.KERNEL_FORMS.items() if v == f.value)
+        return {"block": b.value, "work_target_flops": t.value, "n_items": n.value, "kernel_form": form}
+
+    def set_kernel_form(self, form: str) -> None:
+        """"table" or "specialised" (straight-line points for k <= 4)."""
+        check(_lib.lib().qed_batch_set_kernel_form(self._h, Plan.KERNEL_FORMS[form]), "qed_batch_set_kernel_form")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

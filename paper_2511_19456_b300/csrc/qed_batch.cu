@@ -8,8 +8,11 @@
 // with teams of the item's k (eval_range, the same code as the standalone
 // forward kernel).  A counter reset plus the launch are captured once in a
 // CUDA graph and replayed; per call only the request table (device pointers
-// of momenta and outputs) is copied.  qed_batch_tune times a small grid of
-// block sizes and item sizes on the caller's buffers and keeps the fastest.
+// of momenta and outputs) is copied.  Two kernel forms, as for a plan: the
+// table-driven point evaluation for every k, or the straight-line
+// specialised one for k <= 4 (generated at build time; k = 5 stays
+// table-driven).  qed_batch_tune times every form, block size and item size
+// of a small grid on the caller's buffers and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +29,7 @@ struct qed_batch_s {
   std::vector<qed_plan_t> plans;
   std::vector<long long> n;
   bool mixed = false;
+  int form = QED_KERNEL_SPECIALISED;   // qed_kernel_form of the batched kernel
   int block = 128;
   double work_target = 4e8;      // algorithmic FLOPs per item
   std::vector<BatchDesc> h_desc;
@@ -62,9 +66,20 @@ void free_batch(qed_batch_s* b) {
   delete b;
 }
 
-using BatchFn = void (*)(const BatchDesc*, const BatchItem*, int, unsigned*);
+BatchFn batch_fn(bool mixed, int form) {
+  if (form == QED_KERNEL_SPECIALISED) return batch_spec_kernel(mixed);
+  return mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>;
+}
 
-BatchFn batch_fn(bool mixed) { return mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>; }
+// Shared memory per team of a request's points in a form: the specialised
+// kernel's own layout for k <= 4, else the plan's table kernel layout.
+int team_bytes_of(const qed_plan_s* P, int form) {
+  if (form == QED_KERNEL_SPECIALISED && P->k <= 4) {
+    const SpecKernel sk = spec_forward_kernel(P->k, P->prec == QED_MIXED);
+    if (sk.fn) return sk.team_bytes;
+  }
+  return P->team_bytes;
+}
 
 // Work list, launch shape and graph for the current (block, work_target).
 qed_status configure(qed_batch_s* b) {
@@ -76,7 +91,7 @@ qed_status configure(qed_batch_s* b) {
     const int team = 1 << (P->k + 1);
     if (b->block < team) return QED_EINVAL;
     const int tpc = b->block / team;
-    smem = std::max(smem, (size_t)tpc * P->team_bytes);
+    smem = std::max(smem, (size_t)tpc * team_bytes_of(P, b->form));
     const double fl = (double)std::max<long long>(1, P->sc.flops_algorithmic);
     long long chunk = (long long)(b->work_target / fl);
     chunk = std::max<long long>(tpc, (chunk / tpc) * tpc);
@@ -91,7 +106,7 @@ qed_status configure(qed_batch_s* b) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_status(e);
   if (smem + 64 > (size_t)dev_smem) return QED_EUNSUPPORTED;
-  BatchFn fn = batch_fn(b->mixed);
+  BatchFn fn = batch_fn(b->mixed, b->form);
   // the limit at the device's maximum, for every batch and for
   // qed_batch_eval_static alike: none of them lowers it under another's graph
   int limit = 0;
@@ -192,11 +207,13 @@ qed_status qed_batch_tune(qed_batch_t b, const double* const* d_momenta, double*
   if (cudaEventCreate(&e0) != cudaSuccess) return QED_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return QED_ECUDA; }
   const int blocks[] = {64, 128, 256};
-  const double targets[] = {1e8, 4e8, 1.6e9, 6.4e9};
-  int best_block = b->block;
+  const double targets[] = {1e8, 4e8, 1.6e9};
+  int best_block = b->block, best_form = b->form;
   double best_target = b->work_target, best = 1e300;
+  for (int form : {QED_KERNEL_TABLE, QED_KERNEL_SPECIALISED})
   for (int blk : blocks) {
     for (double tgt : targets) {
+      b->form = form;
       b->block = blk;
       b->work_target = tgt;
       if (configure(b) != QED_OK) continue;
@@ -209,11 +226,12 @@ qed_status qed_batch_tune(qed_batch_t b, const double* const* d_momenta, double*
       if (cudaEventSynchronize(e1) != cudaSuccess) continue;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / 2 < best) { best = ms / 2; best_block = blk; best_target = tgt; }
+      if (ms / 2 < best) { best = ms / 2; best_block = blk; best_target = tgt; best_form = form; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->form = best_form;
   b->block = best_block;
   b->work_target = best_target;
   s = configure(b);
@@ -227,6 +245,24 @@ qed_status qed_batch_info(qed_batch_t b, int* block, double* work_target, long l
   if (block) *block = b->block;
   if (work_target) *work_target = b->work_target;
   if (n_items) *n_items = (long long)b->h_items.size();
+  return QED_OK;
+}
+
+qed_status qed_batch_set_kernel_form(qed_batch_t b, int form) {
+  if (!b || (form != QED_KERNEL_TABLE && form != QED_KERNEL_SPECIALISED)) return QED_EINVAL;
+  const int old = b->form;
+  b->form = form;
+  qed_status s = configure(b);
+  if (s != QED_OK) {
+    b->form = old;
+    configure(b);
+  }
+  return s;
+}
+
+qed_status qed_batch_kernel_form(qed_batch_t b, int* form) {
+  if (!b || !form) return QED_EINVAL;
+  *form = b->form;
   return QED_OK;
 }
 

@@ -50,6 +50,13 @@ qed_batch_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict
   }
 }
 
+using BatchFn = void (*)(const BatchDesc*, const BatchItem*, int, unsigned*);
+
+// The specialised form of the batched kernel (generated with the
+// straight-line forward kernels): the same work-item loop, with the
+// straight-line point evaluation for k <= 4.
+BatchFn batch_spec_kernel(bool mixed);
+
 // The largest dynamic shared memory a launch of fn may ask for: the device's
 // opt-in maximum less the kernel's static shared memory.
 inline cudaError_t max_dynamic_smem(const void* fn, int dev_smem, int* out) {

@@ -487,7 +487,7 @@ int main(int argc, char** argv) {
       << "// the team's lanes with literal photon, polarisation rank, source,\n"
       << "// destination and propagator; the S2 joins of each photon set on the leaf\n"
       << "// layout of qed_spec.cuh.\n"
-      << "#include \"qed_spec.cuh\"\n#include \"qed_plan.hpp\"\n\nnamespace qed {\n\n";
+      << "#include \"qed_spec.cuh\"\n#include \"qed_plan.hpp\"\n#include \"qed_batch.cuh\"\n\nnamespace qed {\n\n";
   std::vector<KernelDesc> kds;
   try {
     for (int k = 1; k <= 4; ++k)
@@ -496,6 +496,70 @@ int main(int argc, char** argv) {
     std::fprintf(stderr, "qed_codegen: %s\n", e.what());
     return 1;
   }
+  // the batched evaluation's specialised form: the persistent work-item loop
+  // of qed_batch_kernel (qed_batch.cuh) with the straight-line points for
+  // k <= 4 and the table-driven ones for k = 5; each item kind is a call of
+  // its own (not inlined), so that registers are allocated per kind rather
+  // than for their union
+  out << "// The batched evaluation (requests of k = 1..5 in one persistent launch),\n"
+      << "// specialised form: the work-item loop of qed_batch_kernel with the\n"
+      << "// straight-line point evaluation above for k <= 4; k = 5 has no\n"
+      << "// specialised kernel and runs the table-driven one.  One item's points\n"
+      << "// per call, each kind of item a function of its own (called, not\n"
+      << "// inlined: registers are allocated per kind, not for their union).\n"
+      << "template <int K, typename Real>\n"
+      << "__device__ __noinline__ void batch_spec_item(const KParams& kp, long long p0, long long p1,\n"
+      << "                                             unsigned char* smem) {\n"
+      << "  constexpr int TEAM = 1 << (K + 1);\n"
+      << "  const int lane = threadIdx.x & (TEAM - 1), team = threadIdx.x / TEAM, tpc = blockDim.x / TEAM;\n";
+  for (int k = 1; k <= 4; ++k) {
+    int tb32 = 0, tb64 = 0;
+    for (const KernelDesc& kd : kds)
+      if (kd.k == k) (kd.mixed ? tb32 : tb64) = kd.team_bytes;
+    out << "  " << (k == 1 ? "" : "else ") << "if constexpr (K == " << k << ") {\n"
+        << "    unsigned char* base = smem + (size_t)team * (sizeof(Real) == 4 ? " << tb32 << " : " << tb64
+        << ");\n"
+        << "    for (long long pt0 = p0; pt0 < p1; pt0 += tpc) {\n"
+        << "      const long long pt = pt0 + team;\n"
+        << "      const bool valid = pt < p1;\n"
+        << "      if constexpr (sizeof(Real) == 4) qed_spec_fwd_k" << k
+        << "_f32_point(kp, lane, valid ? pt : p1 - 1, valid, base);\n"
+        << "      else qed_spec_fwd_k" << k << "_f64_point(kp, lane, valid ? pt : p1 - 1, valid, base);\n"
+        << "    }\n"
+        << "  }\n";
+  }
+  out << "  else {\n"
+      << "    eval_range<K, true, Real, TEAM, 1>(kp, p0, p1, (long long)(blockDim.x / TEAM), smem);\n"
+      << "  }\n"
+      << "}\n\n"
+      << "template <typename Real>\n"
+      << "__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1)\n"
+      << "qed_batch_spec_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict__ items,\n"
+      << "                      int n_items, unsigned* counter) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+      << "  __shared__ int s_item;\n"
+      << "  for (;;) {\n"
+      << "    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);\n"
+      << "    __syncthreads();\n"
+      << "    const int it = s_item;\n"
+      << "    __syncthreads();\n"
+      << "    if (it >= n_items) break;\n"
+      << "    const BatchItem item = items[it];\n"
+      << "    const KParams& kp = reqs[item.req].kp;\n"
+      << "    switch (item.k) {\n"
+      << "      case 1: batch_spec_item<1, Real>(kp, item.p0, item.p1, smem); break;\n"
+      << "      case 2: batch_spec_item<2, Real>(kp, item.p0, item.p1, smem); break;\n"
+      << "      case 3: batch_spec_item<3, Real>(kp, item.p0, item.p1, smem); break;\n"
+      << "      case 4: batch_spec_item<4, Real>(kp, item.p0, item.p1, smem); break;\n"
+      << "      case 5: batch_spec_item<5, Real>(kp, item.p0, item.p1, smem); break;\n"
+      << "      default: break;\n"
+      << "    }\n"
+      << "    __syncthreads();\n"
+      << "  }\n"
+      << "}\n\n"
+      << "BatchFn batch_spec_kernel(bool mixed) {\n"
+      << "  return mixed ? qed_batch_spec_kernel<float> : qed_batch_spec_kernel<double>;\n"
+      << "}\n\n";
   out << "SpecKernel spec_forward_kernel(int k, bool mixed) {\n";
   for (const KernelDesc& kd : kds)
     out << "  if (k == " << kd.k << " && mixed == " << (kd.mixed ? "true" : "false") << ") return {" << kd.name

@@ -1,6 +1,7 @@
 """Batched persistent launch: requests of k = 1..5 with uneven point counts in
 one graph launch give the same |M|^2 as one standalone launch per request
-(bit for bit: same per-point code), and match the oracle on samples."""
+(bit for bit: same per-point code, in either kernel form), and match the
+oracle on samples."""
 import ctypes
 
 import numpy as np
@@ -22,19 +23,23 @@ def make_inputs(seed0=700):
     return moms
 
 
+@pytest.mark.parametrize("form", ["table", "specialised"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_standalone_and_oracle(orc, precision):
+def test_batch_matches_standalone_and_oracle(orc, precision, form):
     plans = {k: Plan(k, precision=precision) for k in range(1, 6)}
     moms = make_inputs()
     batch = Batch([plans[k] for k, _, _ in REQS], [n for _, n, _ in REQS])
+    assert batch.info()["kernel_form"] == "specialised"   # a new batch's form
+    batch.set_kernel_form(form)
+    assert batch.info()["kernel_form"] == form
     outs = batch.eval(moms)
     torch.cuda.synchronize()
     for (k, n, _), m, o in zip(REQS, moms, outs):
         if n == 0:
             continue
-        # the batch runs the table-driven kernel code of every k: bit for bit
-        # the standalone plan in that form
-        plans[k].set_kernel_form("table")
+        # the batch runs the point code of the standalone plan in the same
+        # form (k = 5 has only the table form): bit for bit
+        plans[k].set_kernel_form(form if k <= 4 else "table")
         ref = plans[k].eval(m)
         torch.cuda.synchronize()
         assert torch.equal(o, ref), (k, n)
@@ -58,6 +63,7 @@ def test_batch_tune_and_replay():
     ms = batch.tune(moms)
     info = batch.info()
     assert ms > 0 and info["block"] in (64, 128, 256) and info["n_items"] > 0
+    assert info["kernel_form"] in ("table", "specialised")
     outs = batch.outputs()
     for _ in range(3):
         batch.eval(moms, outs)
@@ -115,20 +121,24 @@ def _static_call(plans, n, moms, outs):
     return L.qed_batch_eval_static(ph, nreq, nn, pm, po, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("entry", ["qed_batch_eval", "qed_batch_eval_static"])
+@pytest.mark.parametrize("entry", ["qed_batch_eval", "qed_batch_eval_table", "qed_batch_eval_static"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_seeded_batched_stream_vs_oracle(seeded_stream, seeded_stream_oracle, entry, precision):
     """All 64 requests (10.9 M points) in one persistent launch, then each
-    request's first points against the oracle at the per-point bounds."""
+    request's first points against the oracle at the per-point bounds:
+    qed_batch_eval in its tuned (mixed) or default (FP64) form and in the
+    table form, and the allocation-free entry point."""
     from tests.test_gpu_parity import check_mixed_median
     reqs, moms = seeded_stream
     plans = {k: Plan(k, precision=precision) for k in range(1, 6)}
     req_plans = [plans[r["k"]] for r in reqs]
     n = [r["n_points"] for r in reqs]
     d = [torch.from_numpy(m).cuda() for m in moms]
-    if entry == "qed_batch_eval":
+    if entry.startswith("qed_batch_eval") and entry != "qed_batch_eval_static":
         batch = Batch(req_plans, n)
-        if precision == "mixed":
+        if entry == "qed_batch_eval_table":
+            batch.set_kernel_form("table")
+        elif precision == "mixed":
             batch.tune(d, batch.outputs())
         outs = batch.eval(d)
     else:
@@ -149,3 +159,11 @@ def test_seeded_batched_stream_vs_oracle(seeded_stream, seeded_stream_oracle, en
           f"median rel {np.median(rel):.3e} max {rel.max():.3e} (kappa max {kap.max():.1f})")
     if precision == "mixed":
         check_mixed_median(rel, kap)
+
+
+def test_batch_form_rejects_unknown():
+    L = _lib.lib()
+    batch = Batch([Plan(2)], [10])
+    assert L.qed_batch_set_kernel_form(batch._h, 2) == _lib.QED_EINVAL
+    assert L.qed_batch_set_kernel_form(None, 0) == _lib.QED_EINVAL
+    assert batch.info()["kernel_form"] == "specialised"
