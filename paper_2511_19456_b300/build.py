@@ -20,9 +20,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqedm2.so")
 GEN = os.path.join(BUILD, "qed_spec_gen.cu")
 SOURCES = ["dag.cpp", "qed_api.cpp", "qed_fwd.cu", "qed_rw.cu", "abc_kernel.cu", "qed_tape.cu", "qed_adj.cu",
-           "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu", "qed_fix.cu"]
+           "qed_batch.cu", "qed_noalloc.cu", "qed_gen.cu", "qed_peak.cu", "qed_fix.cu", "qed_radj.cu"]
 HEADERS = ["dag.hpp", "qed_types.h", "qed_device.cuh", "qed_team.cuh", "qed_eval.cuh", "qed_plan.hpp", "qed_batch.cuh",
-           "qed_spec.cuh"]
+           "qed_spec.cuh", "qed_adjoint.cuh"]
 GENERATOR = ["qed_codegen.cpp", "dag.cpp", "dag.hpp", "qed_types.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr",

@@ -37,56 +37,19 @@
 // all contend for the same FP64 words.
 #include <cuda_runtime.h>
 
+#include "qed_adjoint.cuh"
 #include "qed_team.cuh"
 
 namespace qed {
 
 namespace {
 
-// Real parts of the bilinears s_mu = sum_ab a_a gamma^mu_ab b_b (mu = 0..3,
-// Dirac representation) and u = sum_c a_c b_c, for complex 4-vectors a, b
-// stored as 8 reals.  Q, D and eps are real, so df = 2 Re(...) needs only
-// these.  Each is one FMA chain over its four products:
-//   gamma^0 = diag(1, 1, -1, -1):             s_0 = a0 b0 + a1 b1 - a2 b2 - a3 b3
-//   gamma^i = [[0, sigma^i], [-sigma^i, 0]]:  s_i = a_u sigma^i b_l - a_l sigma^i b_u
-//     x sigma^1 y = x0 y1 + x1 y0   ->  s_1 = a0 b3 + a1 b2 - a2 b1 - a3 b0
-//     x sigma^2 y = i (x1 y0 - x0 y1) -> Re s_2 = Im(a0 b3 - a1 b2 + a3 b0 - a2 b1)
-//     x sigma^3 y = x0 y0 - x1 y1   ->  s_3 = a0 b2 - a1 b3 - a2 b0 + a3 b1
-// acc + g Re(a_i b_j) and acc + g Im(a_i b_j), g = +-1
-template <typename Real>
-__device__ __forceinline__ Real fre(const Real* a, int i, const Real* b, int j, Real g, Real acc) {
-  return fma(g * a[2 * i], b[2 * j], fma(-g * a[2 * i + 1], b[2 * j + 1], acc));
-}
-template <typename Real>
-__device__ __forceinline__ Real fim(const Real* a, int i, const Real* b, int j, Real g, Real acc) {
-  return fma(g * a[2 * i], b[2 * j + 1], fma(g * a[2 * i + 1], b[2 * j], acc));
-}
-
-template <typename Real>
-__device__ __forceinline__ Real bil_s0(const Real* a, const Real* b) {
-  const Real one = 1, mone = -1;
-  return fre(a, 3, b, 3, mone, fre(a, 2, b, 2, mone, fre(a, 1, b, 1, one, fre(a, 0, b, 0, one, (Real)0))));
-}
-template <typename Real>
-__device__ __forceinline__ Real bil_s1(const Real* a, const Real* b) {
-  const Real one = 1, mone = -1;
-  return fre(a, 3, b, 0, mone, fre(a, 2, b, 1, mone, fre(a, 1, b, 2, one, fre(a, 0, b, 3, one, (Real)0))));
-}
-template <typename Real>
-__device__ __forceinline__ Real bil_s2(const Real* a, const Real* b) {
-  const Real one = 1, mone = -1;
-  return fim(a, 2, b, 1, mone, fim(a, 3, b, 0, one, fim(a, 1, b, 2, mone, fim(a, 0, b, 3, one, (Real)0))));
-}
-template <typename Real>
-__device__ __forceinline__ Real bil_s3(const Real* a, const Real* b) {
-  const Real one = 1, mone = -1;
-  return fre(a, 3, b, 1, one, fre(a, 2, b, 0, mone, fre(a, 1, b, 3, mone, fre(a, 0, b, 2, one, (Real)0))));
-}
-template <typename Real>
-__device__ __forceinline__ Real bil_u(const Real* a, const Real* b) {
-  const Real one = 1;
-  return fre(a, 3, b, 3, one, fre(a, 2, b, 2, one, fre(a, 1, b, 1, one, fre(a, 0, b, 0, one, (Real)0))));
-}
+using adjb::bil_s0;
+using adjb::bil_s1;
+using adjb::bil_s2;
+using adjb::bil_s3;
+using adjb::bil_u;
+using adjb::dpol;
 
 template <typename Real>
 __device__ __forceinline__ void atomic_add_cur(Real* p, int nv, const Real x[8]) {
@@ -340,37 +303,6 @@ __device__ __forceinline__ void flush_partials(const KParams& p, int set, int la
       e[i] = 0.f;
     }
   }
-}
-
-// d eps_pol / d k_a (a = x, y, z) for the real linear polarisations; zero on
-// the z axis, where the basis is fixed by convention.
-__device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) {
-  const double kx = k[1], ky = k[2], kz = k[3];
-  const double kt2 = kx * kx + ky * ky;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d[a][i] = 0.0;
-  if (kt2 == 0.0) return;
-  const double kt = sqrt(kt2);
-  if (pbit) {
-    // eps_2 = (-ky, kx, 0) / kT
-    const double c = 1.0 / (kt2 * kt);
-    d[0][0] = kx * ky * c; d[0][1] = ky * ky * c;
-    d[1][0] = -kx * kx * c; d[1][1] = -kx * ky * c;
-    return;
-  }
-  // eps_1 = g (kx kz, ky kz, -kT^2), g = 1 / (K kT)
-  const double K2 = kt2 + kz * kz;
-  const double K = sqrt(K2);
-  const double g = 1.0 / (K * kt);
-  const double num[3] = {kx * kz, ky * kz, -kt2};
-  const double dg[3] = {-g * (kx / K2 + kx / kt2), -g * (ky / K2 + ky / kt2), -g * kz / K2};
-  const double dn[3][3] = {{kz, 0.0, -2.0 * kx}, {0.0, kz, -2.0 * ky}, {kx, ky, 0.0}};
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d[a][i] = g * dn[a][i] + num[i] * dg[a];
 }
 
 }  // namespace

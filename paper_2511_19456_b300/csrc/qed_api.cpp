@@ -54,6 +54,8 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_dep_tab);
   cudaFree(p->d_part_tab);
   cudaFree(p->d_fix_items);
+  cudaFree(p->d_radj_masks);
+  cudaFree(p->d_radj_slot);
   cudaFree(p->d_stage);
   if (p->ev_scratch) cudaEventDestroy(p->ev_scratch);
   for (int i = 0; i < 2; ++i) {
@@ -188,7 +190,62 @@ int assign_partial_slots(Schedule& sc, std::vector<uint16_t>* tab) {
   return (int)n_part;
 }
 
+// The adjoint on the rewritten DAG (qed_radj.cu): one current per photon
+// subset and side, kept for the whole point with its adjoint.  Tables: the
+// subsets of every node, column side then row side, level by level in
+// increasing mask order, and the first current of each (side, subset).
+// Sets *done when the plan takes it; leaves the plan alone where the kernel
+// does not exist or a team does not fit in shared memory.
+qed_status setup_radj(qed_plan_s* P, bool mixed, int dev_smem, int sms, bool* done) {
+  *done = false;
+  const KernelChoice kc = radj_kernel(P->k, P->summed, mixed);
+  if (!kc.fn) return QED_OK;
+  const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
+  std::vector<int> masks, slot(2u << n, -1);
+  int lev[2][10] = {{0}};
+  int next = 0;
+  for (int side = 0; side < 2; ++side) {
+    const int top = side == 0 ? h : r;
+    for (int l = 1; l <= 9; ++l) {
+      lev[side][l] = (int)masks.size();
+      if (l > top) continue;
+      for (int T = 1; T < (1 << n); ++T) {
+        if (__builtin_popcount(T) != l) continue;
+        masks.push_back(T);
+        slot[(side << n) | T] = next;
+        next += P->summed ? (2 << l) : 1;
+      }
+    }
+  }
+  const int team = kc.team, block = std::max(team, 32);
+  const size_t smem = (size_t)(block / team) * radj_layout(k, mixed ? 4 : 8, next, P->summed, team).bytes;
+  if (smem > (size_t)dev_smem) return QED_OK;
+  cudaError_t e = upload(&P->d_radj_masks, masks);
+  if (e == cudaSuccess) e = upload(&P->d_radj_slot, slot);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kc.fn, block, smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (per_sm < 1) return QED_OK;
+  std::memcpy(P->radj_lev, lev, sizeof(lev));
+  P->radj_ncur = next;
+  P->radj = true;
+  P->kc_adj = kc;
+  P->block_adj = block;
+  P->smem_adj = smem;
+  P->grid_adj = per_sm * sms;
+  P->has_adj = true;
+  *done = true;
+  return QED_OK;
+}
+
 qed_status setup_adjoint(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
+  {
+    bool done = false;
+    const qed_status rs = setup_radj(P, mixed, dev_smem, sms, &done);
+    if (rs != QED_OK || done) return rs;
+  }
   const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
   P->kc_adj = adjoint_kernel(k, P->summed, mixed);
   if (!P->kc_adj.fn) return QED_OK;
@@ -959,6 +1016,12 @@ qed_status launch_grad(qed_plan_t P, const double* d_momenta, long long n, doubl
   kp.adj_scratch_team = P->adj_scratch_team;
   kp.part_tab = P->d_part_tab;
   kp.n_part = P->n_part;
+  if (P->radj) {
+    kp.radj_masks = P->d_radj_masks;
+    kp.radj_slot = P->d_radj_slot;
+    std::memcpy(kp.radj_lev, P->radj_lev, sizeof(kp.radj_lev));
+    kp.ncur = P->radj_ncur;
+  }
   const int tpc = P->block_adj / P->kc_adj.team;
   const long long need = (n + tpc - 1) / tpc;
   const int grid = (int)std::min<long long>(need, P->grid_adj);

@@ -34,6 +34,9 @@ SpecKernel spec_forward_kernel(int k, bool mixed);
 // One fixed state, FP32-mixed, register-join form (qed_fix.cu), k = 1..6;
 // fn == nullptr otherwise.
 KernelChoice fixed_join_kernel(int k);
+// Adjoint on the distributively rewritten DAG (qed_radj.cu): spin-summed
+// k <= 5 and one fixed state k <= 7; fn == nullptr otherwise.
+KernelChoice radj_kernel(int k, bool summed, bool mixed);
 const char* spec_version();
 }  // namespace qed
 
@@ -105,6 +108,12 @@ struct qed_plan_s {
   // one fixed state, mixed: the register-join form's items (KParams::fix_*)
   int* d_fix_items = nullptr;
   int fix_ngroups = 0, fix_group[9] = {0}, fix_set_off = 0, fix_rbase = 0, fix_ncur = 0;
+  // the adjoint on the rewritten DAG (KParams::radj_*), when kc_adj is it
+  bool radj = false;
+  int* d_radj_masks = nullptr;
+  int* d_radj_slot = nullptr;
+  int radj_lev[2][10] = {{0}};
+  int radj_ncur = 0;
   int n_part = 0;
   int device = 0;
   // staging for qed_eval_host (one call at a time per plan: stage_lock)

@@ -1,0 +1,562 @@
+// Adjoint kernels on the distributively rewritten DAG: |M|^2 and
+// d|M|^2 / d k_j for the outgoing photons' 3-momenta (slots 3..k+2, energies
+// on shell E_j = |k_j|; p, k_0 and p' held fixed) -- the same function and
+// outputs as qed_adj.cu, whose reverse pass walks the node-reduced tries.
+//
+// The rewritten DAG (term rewriting by distributivity, which the paper
+// proposes as a further DAG operation, App. C): one current per photon
+// subset and side,
+//   column:  J_T = sum_{j in T} eps/_j K_{T\j},  K_{} = u(p),
+//            K_T = S(Q_T) J_T for |T| < h; J_S (|S| = h) is a left leaf;
+//   row:     I_U = sum_{j in U} G_{U\j} eps/_j,   G_{} = ubar(p'),
+//            G_U = I_U S(Q_{all\U}) for |U| <= r (for |U| = r the hoisted
+//            propagation half of S2);
+//   M_l = sum_{|S| = h} G_{all\S}[l_R] . J_S[l_L].
+// Expanding the sums gives back every diagram's chain (Sec. I-D, Eq. 1), so
+// M_l and all its derivatives are those of the node-reduced DAG; each
+// subset is built once per point and kept in shared memory, and the reverse
+// pass visits each subset once.
+//
+// Reverse mode, with f = sum_l |M_l|^2, seeds Mbar_l = conj(M_l) and the
+// bilinear adjoints of qed_adj.cu (sum_l conj(M_l) dM_l = sum zbar . dz):
+//   1. transposed joins: Jbar_S[vL] = sum_vR Mbar_l G_{S^c}[vR] and
+//      Gbar_{S^c}[vR] = sum_vL Mbar_l J_S[vL]; every leaf is in one join;
+//   2. the levels, deepest first, both sides in one phase; a node gathers
+//      its adjoint from the pre-propagator adjoints of its parents (the
+//      subsets one photon larger), so each adjoint has one writer:
+//        column node T:  Kbar_T = sum_{j not in T} Jbar_{T+j} eps/_j,
+//                        Jbar_T = Kbar_T S(Q_T);
+//        row node U:     Gbar_U = sum_{j not in U} eps/_j Ibar_{U+j},
+//                        Ibar_U = S(Q_{all\U}) Gbar_U;
+//      with the propagator terms Re s_mu = Re(ybar gamma^mu w) (w the
+//      node's sum before its propagator, recomputed from its inputs) and
+//      Re u = Re(ybar . y), and the polarisation terms -Re(wbar gamma^i x)
+//      of the node's own vertices;
+//   3. parameter terms -> photon momenta, as in qed_adj.cu.
+// The propagator terms of the lanes that share a node are summed by
+// shuffles, then added to FP64 accumulators by one lane; the polarisation
+// terms go to per-lane accumulators (no atomics), summed at the end.
+#include <cuda_runtime.h>
+
+#include "qed_adjoint.cuh"
+#include "qed_plan.hpp"
+#include "qed_team.cuh"
+
+namespace qed {
+
+namespace {
+
+using adjb::bil_s0;
+using adjb::bil_s1;
+using adjb::bil_s2;
+using adjb::bil_s3;
+using adjb::bil_u;
+using adjb::dpol;
+
+// y += SIGN (sigma . a) x for a real 3-vector a and a complex 2-vector x
+// (column form; the row form x (sigma . a) is the column form of
+// (a_x, -a_y, a_z)), as FMA chains.
+template <int SIGN, typename R>
+__device__ __forceinline__ void pauli_fma(R ax, R ay, R az, const R x[4], R y[4]) {
+  ax *= SIGN; ay *= SIGN; az *= SIGN;
+  y[0] = fma(az, x[0], fma(ax, x[2], fma(ay, x[3], y[0])));
+  y[1] = fma(az, x[1], fma(ax, x[3], fma(-ay, x[2], y[1])));
+  y[2] = fma(ax, x[0], fma(-ay, x[1], fma(-az, x[2], y[2])));
+  y[3] = fma(ax, x[1], fma(ay, x[0], fma(-az, x[3], y[3])));
+}
+
+// acc += eps/ x (column) ...
+template <typename R>
+__device__ __forceinline__ void vacc_col(const R e[3], const R x[8], R acc[8]) {
+  pauli_fma<-1>(e[0], e[1], e[2], x + 4, acc);
+  pauli_fma<1>(e[0], e[1], e[2], x, acc + 4);
+}
+// ... and acc += x eps/ (row), eps/ = [[0, -s.e], [s.e, 0]]
+template <typename R>
+__device__ __forceinline__ void vacc_row(const R e[3], const R x[8], R acc[8]) {
+  pauli_fma<1>(e[0], -e[1], e[2], x + 4, acc);
+  pauli_fma<-1>(e[0], -e[1], e[2], x, acc + 4);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_e3(const R* p, R e[3]) {
+  e[0] = p[0]; e[1] = p[1]; e[2] = p[2];
+}
+
+// The bits of c selected by mask, packed into the low bits, and the inverse.
+template <int N>
+__device__ __forceinline__ unsigned pext_n(unsigned c, unsigned mask) {
+  unsigned r = 0;
+  int o = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if ((mask >> j) & 1u) { r |= ((c >> j) & 1u) << o; ++o; }
+  return r;
+}
+template <int N>
+__device__ __forceinline__ unsigned pdep_n(unsigned x, unsigned mask) {
+  unsigned r = 0;
+  int o = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if ((mask >> j) & 1u) { r |= ((x >> o) & 1u) << j; ++o; }
+  return r;
+}
+
+__device__ __forceinline__ int slot_of(const KParams& p, int n, int side, unsigned mask) {
+  return __ldg(p.radj_slot + (side << n) + (int)mask);
+}
+
+// Spin variant of a node without / with the polarisation bit b (bit 0 is the
+// electron helicity, bit 1 + r the polarisation of the set's photon of rank r).
+__device__ __forceinline__ int drop_bit(int v, int b) { return (v & ((1 << b) - 1)) | ((v >> (b + 1)) << b); }
+__device__ __forceinline__ int ins_bit(int v, int b, int pol) {
+  return (v & ((1 << b) - 1)) | (pol << b) | ((v >> b) << (b + 1));
+}
+
+// Input x_j of the vertex of photon j in node (side, T), variant v: the
+// current of T \ j (variant without j's bit) or the external spinor; also
+// returns j's polarisation in this variant.
+template <int N, bool SUMMED, typename Real>
+__device__ __forceinline__ void vertex_input(const KParams& p, int side, unsigned T, int j, int b, int v,
+                                             const Real* s_spin, const Real* s_cur, Real x[8], int& pol) {
+  int vp;
+  if constexpr (SUMMED) {
+    pol = (v >> b) & 1;
+    vp = drop_bit(v, b);
+  } else {
+    pol = (int)((p.fixed_pol_bits >> j) & 1u);
+    vp = 0;
+  }
+  const unsigned Tm = T & ~(1u << j);
+  if (Tm == 0) {
+    const int e = SUMMED ? vp : (side == 0 ? p.fixed_sin : p.fixed_sout);
+    load8(s_spin + (side * 2 + e) * 8, x);
+  } else {
+    load_cur(s_cur, slot_of(p, N, side, Tm), 0, vp, x);
+  }
+}
+
+// The node's sum of vertex terms before its propagator: J_T (column) or I_U (row).
+template <int N, bool SUMMED, typename Real>
+__device__ __forceinline__ void vertex_sum(const KParams& p, int side, unsigned T, int v, const Real* s_eps,
+                                           const Real* s_spin, const Real* s_cur, Real w[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) w[c] = (Real)0;
+  int t = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (!((T >> j) & 1u)) continue;
+    const int b = 1 + t++;
+    Real x[8];
+    int pol;
+    vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, s_cur, x, pol);
+    Real ev[3];
+    load_e3(s_eps + (j * 2 + pol) * 4, ev);
+    if (side == 0) vacc_col(ev, x, w); else vacc_row(ev, x, w);
+  }
+}
+
+}  // namespace
+
+// Up to 128 registers per thread in FP32, 255 in FP64 (one warp per block
+// for teams of up to 32 lanes, one team per block above).
+template <int K, bool SUMMED, typename Real, int TEAM>
+__global__ void __launch_bounds__(TEAM > 32 ? TEAM : 32,
+                                  sizeof(Real) == 8 ? 1 : 65536 / ((TEAM > 32 ? TEAM : 32) * 128))
+qed_radj_kernel(const KParams p) {
+  constexpr int N = K + 1;
+  constexpr int H = (N + 1) / 2;
+  constexpr int R = N - H;
+  constexpr int NSUB = 1 << N;
+  constexpr unsigned ALL = (1u << N) - 1;
+  constexpr int LMAX = H > R ? H : R;
+  static_assert(!SUMMED || TEAM == (1 << N), "one lane per polarisation pattern");
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const RadjLayout A = radj_layout(K, (int)sizeof(Real), p.ncur, SUMMED, TEAM);
+  const TeamLayout& L = A.fwd;
+  const int lane = threadIdx.x & (TEAM - 1);
+  const int team = threadIdx.x / TEAM;
+  const int tpc = blockDim.x / TEAM;
+  unsigned char* base = smem + (size_t)team * A.bytes;
+  double* s_mom = reinterpret_cast<double*>(base + L.mom);
+  Real* s_q = reinterpret_cast<Real*>(base + L.q);
+  Real* s_eps = reinterpret_cast<Real*>(base + L.eps);
+  Real* s_spin = reinterpret_cast<Real*>(base + L.spin);
+  double* s_red = reinterpret_cast<double*>(base + L.red);
+  Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
+  Real* s_adj = reinterpret_cast<Real*>(base + A.adj);
+  Real* s_mbar = reinterpret_cast<Real*>(base + A.mbar);
+  double* s_acc_s = reinterpret_cast<double*>(base + A.acc_s);
+  double* s_acc_e = reinterpret_cast<double*>(base + A.acc_e);
+  double* s_kbar = reinterpret_cast<double*>(base + A.kbar);
+  Real* s_el = reinterpret_cast<Real*>(base + A.elane) + lane * N * 6;   // this lane's polarisation terms
+
+  const int* masks = p.radj_masks;
+  const int nsets = p.radj_lev[0][H + 1] - p.radj_lev[0][H];
+  const int* set_masks = masks + p.radj_lev[0][H];
+
+  for (long long pt0 = (long long)blockIdx.x * tpc; pt0 < p.n; pt0 += (long long)gridDim.x * tpc) {
+    const long long pt = pt0 + team;
+    const bool valid = pt < p.n;
+    const long long ptc = valid ? pt : p.n - 1;
+
+    // ---- forward: external states, propagators, then the subset currents
+    point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin,
+                               reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
+    for (int l = 1; l <= LMAX; ++l) {
+      const int lg = SUMMED ? l + 1 : 0;
+      const int cl = l <= H ? p.radj_lev[0][l + 1] - p.radj_lev[0][l] : 0;
+      const int cr = l <= R ? p.radj_lev[1][l + 1] - p.radj_lev[1][l] : 0;
+      const int totl = cl << lg, tot = (cl + cr) << lg;
+      for (int it = lane; it < tot; it += TEAM) {
+        const int side = it < totl ? 0 : 1;
+        const int q = side ? it - totl : it;
+        const unsigned T = (unsigned)__ldg(masks + p.radj_lev[side][l] + (q >> lg));
+        const int v = q & ((1 << lg) - 1);
+        Real w[8];
+        vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, s_cur, w);
+        const unsigned post = side == 0 ? (l < H ? T : 0u) : (ALL & ~T);
+        const int dst = slot_of(p, N, side, T);
+        if (post) {
+          Real z[8];
+          if (side == 0) prop_col(s_q + post * 5, w, z); else prop_row(s_q + post * 5, w, z);
+          store_cur(s_cur, dst, 0, v, z);
+        } else {
+          store_cur(s_cur, dst, 0, v, w);
+        }
+      }
+      team_sync<TEAM>();
+    }
+
+    // ---- the joins: M_l = sum_S G_{S^c}[vR] . J_S[vL]
+    Acc<Real> acc[SUMMED ? 4 : 1];
+    if constexpr (SUMMED) {
+      const unsigned c = (unsigned)lane;
+      for (int s = 0; s < nsets; ++s) {
+        const unsigned S = (unsigned)__ldg(set_masks + s), Sc = ALL & ~S;
+        const int vl = (int)pext_n<N>(c, S) << 1, vr = (int)pext_n<N>(c, Sc) << 1;
+        const int ls = slot_of(p, N, 0, S), rs = slot_of(p, N, 1, Sc);
+        Real lc[2][8], rw[2][8];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          load_cur(s_cur, ls, 0, vl + e, lc[e]);
+          load_cur(s_cur, rs, 0, vr + e, rw[e]);
+        }
+#pragma unroll
+        for (int si = 0; si < 2; ++si)
+#pragma unroll
+          for (int so = 0; so < 2; ++so) {
+            Real yr = (Real)0, yi = (Real)0;
+            dot_acc(rw[so], lc[si], yr, yi);
+            acc[si * 2 + so].add(yr, yi);
+          }
+      }
+    } else {
+      for (int s = lane; s < nsets; s += TEAM) {
+        const unsigned S = (unsigned)__ldg(set_masks + s);
+        Real lc[8], rw[8];
+        load_cur(s_cur, slot_of(p, N, 0, S), 0, 0, lc);
+        load_cur(s_cur, slot_of(p, N, 1, ALL & ~S), 0, 0, rw);
+        Real yr = (Real)0, yi = (Real)0;
+        dot_acc(rw, lc, yr, yi);
+        acc[0].add(yr, yi);
+      }
+    }
+
+    // ---- |M|^2 and the seeds conj(M)
+    double m2;
+    if constexpr (SUMMED) {
+      double part = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double re = acc[i].vre(), im = acc[i].vim();
+        part = fma(re, re, fma(im, im, part));
+        const int lam = (i >> 1) | ((i & 1) << 1) | (lane << 2);   // i = 2 si + so
+        s_mbar[2 * lam] = (Real)re;
+        s_mbar[2 * lam + 1] = (Real)(-im);
+      }
+      m2 = team_sum<TEAM>(part, s_red);
+    } else {
+      const double re = team_sum<TEAM>(acc[0].vre(), s_red);
+      const double im = team_sum<TEAM>(acc[0].vim(), s_red);
+      m2 = re * re + im * im;
+      if (lane == 0) { s_mbar[0] = (Real)re; s_mbar[1] = (Real)(-im); }
+    }
+    if (lane == 0 && valid && p.out) p.out[pt] = m2 * p.coupling;
+    for (int i = lane; i < NSUB * 5; i += TEAM) s_acc_s[i] = 0.0;
+    for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < N * 6; ++i) s_el[i] = (Real)0;
+    team_sync<TEAM>();
+
+    // ---- 1. transposed joins, into the leaves' adjoint slots
+    {
+      constexpr int NVL = SUMMED ? 2 << H : 1, NVR = SUMMED ? 2 << R : 1;
+      const int totl = nsets * NVL, tot = nsets * (NVL + NVR);
+      for (int it = lane; it < tot; it += TEAM) {
+        const bool left = it < totl;
+        const int q = left ? it : it - totl;
+        const int s = left ? q / NVL : q / NVR;
+        const int v = left ? q % NVL : q % NVR;
+        const unsigned S = (unsigned)__ldg(set_masks + s), Sc = ALL & ~S;
+        // the other side of the join: the row leaf of S^c for a left item,
+        // the column leaf of S for a right item
+        const unsigned mine = left ? S : Sc, other = left ? Sc : S;
+        const int os = slot_of(p, N, left ? 1 : 0, other);
+        Real o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = (Real)0;
+        if constexpr (SUMMED) {
+          const unsigned cm = pdep_n<N>((unsigned)v >> 1, mine);
+          const int e_mine = v & 1;
+          constexpr int NOTHER_L = 1 << R, NOTHER_R = 1 << H;
+          const int nq = left ? NOTHER_L : NOTHER_R;
+          unsigned co = 0;   // submasks of `other` in increasing order: pdep(q, other)
+          for (int qq = 0; qq < nq; ++qq) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int si = left ? e_mine : e, so = left ? e : e_mine;
+              const int lam = si | (so << 1) | (int)((cm | co) << 2);
+              const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
+              Real x[8];
+              load_cur(s_cur, os, 0, (qq << 1) | e, x);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                o[2 * c] = fma(mr, x[2 * c], fma(-mi, x[2 * c + 1], o[2 * c]));
+                o[2 * c + 1] = fma(mr, x[2 * c + 1], fma(mi, x[2 * c], o[2 * c + 1]));
+              }
+            }
+            co = ((co | ~other) + 1u) & other;
+          }
+        } else {
+          const Real mr = s_mbar[0], mi = s_mbar[1];
+          Real x[8];
+          load_cur(s_cur, os, 0, 0, x);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            o[2 * c] = mr * x[2 * c] - mi * x[2 * c + 1];
+            o[2 * c + 1] = mr * x[2 * c + 1] + mi * x[2 * c];
+          }
+        }
+        store_cur(s_adj, slot_of(p, N, left ? 0 : 1, mine), 0, v, o);
+      }
+    }
+    team_sync<TEAM>();
+
+    // ---- 2. the levels, deepest first
+    for (int l = LMAX; l >= 1; --l) {
+      const int lg = SUMMED ? l + 1 : 0;
+      const int nv = 1 << lg;
+      const int cl = l <= H ? p.radj_lev[0][l + 1] - p.radj_lev[0][l] : 0;
+      const int cr = l <= R ? p.radj_lev[1][l + 1] - p.radj_lev[1][l] : 0;
+      const int totl = cl << lg, tot = (cl + cr) << lg;
+      constexpr int WMAX = TEAM < 32 ? TEAM : 32;
+      const int G = nv < WMAX ? nv : WMAX;   // lanes of one round that share a node
+      for (int b0 = 0; b0 < tot; b0 += TEAM) {
+        // every lane runs the same rounds (the shuffles below)
+        const int it = b0 + lane;
+        const bool ok = it < tot;
+        const int side = it < totl ? 0 : 1;
+        const int q = side ? it - totl : it;
+        const unsigned T = ok ? (unsigned)__ldg(masks + p.radj_lev[side][l] + (q >> lg)) : 0u;
+        const int v = q & (nv - 1);
+        const bool leaf_l = side == 0 && l == H;
+        const unsigned post = side == 0 ? (l < H ? T : 0u) : (ALL & ~T);
+        Real ps[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) ps[c] = (Real)0;
+        if (ok) {
+          const int my = slot_of(p, N, side, T);
+          // the node's output adjoint ybar: from the joins (leaves) or
+          // gathered from the parents' pre-propagator adjoints
+          Real yb[8];
+          if (l == (side ? R : H)) {
+            load_cur(s_adj, my, 0, v, yb);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) yb[c] = (Real)0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              if ((T >> j) & 1u) continue;
+              const unsigned Tp = T | (1u << j);
+              const int bp = 1 + __popc(T & ((1u << j) - 1u));
+              const int ps_slot = slot_of(p, N, side, Tp);
+#pragma unroll
+              for (int pol = 0; pol < (SUMMED ? 2 : 1); ++pol) {
+                const int pl = SUMMED ? pol : (int)((p.fixed_pol_bits >> j) & 1u);
+                const int vpar = SUMMED ? ins_bit(v, bp, pol) : 0;
+                Real wb[8], ev[3];
+                load_cur(s_adj, ps_slot, 0, vpar, wb);
+                load_e3(s_eps + (j * 2 + pl) * 4, ev);
+                // transposed vertex: column x -> eps/ x gives xbar = wbar eps/
+                if (side == 0) vacc_row(ev, wb, yb); else vacc_col(ev, wb, yb);
+              }
+            }
+          }
+          // through the propagator: wbar = ybar S (column) or S ybar (row),
+          // and its parameter terms
+          Real wb[8];
+          if (post) {
+            const Real* P = s_q + post * 5;
+            if (side == 0) prop_row(P, yb, wb); else prop_col(P, yb, wb);
+            Real w[8], y[8];
+            vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, s_cur, w);
+            load_cur(s_cur, my, 0, v, y);
+            if (side == 0) {
+              ps[0] = bil_s0(yb, w); ps[1] = bil_s1(yb, w); ps[2] = bil_s2(yb, w); ps[3] = bil_s3(yb, w);
+              ps[4] = bil_u(yb, y);
+            } else {
+              ps[0] = bil_s0(w, yb); ps[1] = bil_s1(w, yb); ps[2] = bil_s2(w, yb); ps[3] = bil_s3(w, yb);
+              ps[4] = bil_u(y, yb);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) wb[c] = yb[c];
+          }
+          // polarisation terms of the node's own vertices: -Re(wbar g^i x)
+          // (column) or -Re(x g^i wbar) (row), per photon and polarisation
+          int t = 0;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            if (!((T >> j) & 1u)) continue;
+            const int b = 1 + t++;
+            Real x[8];
+            int pol;
+            vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, s_cur, x, pol);
+            Real* E = s_el + j * 6 + pol * 3;
+            if (side == 0) {
+              E[0] -= bil_s1(wb, x); E[1] -= bil_s2(wb, x); E[2] -= bil_s3(wb, x);
+            } else {
+              E[0] -= bil_s1(x, wb); E[1] -= bil_s2(x, wb); E[2] -= bil_s3(x, wb);
+            }
+          }
+          if (!leaf_l) store_cur(s_adj, my, 0, v, wb);
+        }
+        // the propagator terms of one node's variants: summed over its lanes,
+        // added to the FP64 accumulators by the first
+        for (int off = 1; off < G; off <<= 1)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) ps[c] += __shfl_xor_sync(0xffffffffu, ps[c], off);
+        if (ok && post && (v & (G - 1)) == 0) {
+          double* Ac = s_acc_s + post * 5;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) atomicAdd(Ac + c, (double)ps[c]);
+        }
+      }
+      team_sync<TEAM>();
+    }
+
+    // polarisation terms: the lanes' sums
+    {
+      const Real* el = reinterpret_cast<const Real*>(base + A.elane);
+      for (int i = lane; i < N * 6; i += TEAM) {
+        double a = 0.0;
+        for (int ln = 0; ln < TEAM; ++ln) a += (double)el[ln * N * 6 + i];
+        s_acc_e[i] = a;
+      }
+    }
+    team_sync<TEAM>();
+
+    // ---- 3. parameters -> outgoing photon momenta (FP64)
+#pragma unroll 1
+    for (int mask = lane; mask < NSUB; mask += TEAM) {
+      if (mask == 0 || mask == (int)ALL) continue;
+      double q0 = s_mom[0], q1 = s_mom[1], q2 = s_mom[2], q3 = s_mom[3];
+      for (int j = 0; j < N; ++j) {
+        if (!(mask & (1 << j))) continue;
+        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
+        if (j == 0) { q0 += kj[0]; q1 += kj[1]; q2 += kj[2]; q3 += kj[3]; }
+        else        { q0 -= kj[0]; q1 -= kj[1]; q2 -= kj[2]; q3 -= kj[3]; }
+      }
+      double D = __dmul_rn(q0, q0);
+      D = __dsub_rn(D, __dmul_rn(q1, q1));
+      D = __dsub_rn(D, __dmul_rn(q2, q2));
+      D = __dsub_rn(D, __dmul_rn(q3, q3));
+      D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
+      // df/dQ_T^mu = 2 eta_mu (s_mu - 2 Q^mu u) / D, in place of the subset's accumulator
+      double* Ac = s_acc_s + mask * 5;
+      const double Q[4] = {q0, q1, q2, q3};
+      const double two_inv_d = 2.0 / D;
+      double qb[4];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        const double eta = mu == 0 ? 1.0 : -1.0;
+        qb[mu] = eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) * two_inv_d;
+      }
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) Ac[mu] = qb[mu];
+    }
+    team_sync<TEAM>();
+    // Q_T = p + k_0 - sum_{j in T, j >= 1} k_j: df/dk_j^mu = -sum over the
+    // subsets T that contain j of df/dQ_T^mu, one lane per (j, mu)
+    for (int it = lane; it < K * 4; it += TEAM) {
+      const int j = 1 + (it >> 2), mu = it & 3;
+      const int lo = (1 << j) - 1;
+      double a = 0.0;
+#pragma unroll 1
+      for (int r = 0; r < (1 << (N - 1)) - 1; ++r)   // r = 2^(n-1) - 1 would be the full set
+        a += s_acc_s[(((r >> j) << (j + 1)) | (1 << j) | (r & lo)) * 5 + mu];
+      s_kbar[4 * j + mu] = -a;
+    }
+    team_sync<TEAM>();
+    for (int it = lane; it < 2 * N; it += TEAM) {
+      const int j = it >> 1, pb = it & 1;
+      if (j == 0) continue;
+      const double* E = s_acc_e + (j * 2 + pb) * 3;
+      double d[3][3];
+      dpol(s_mom + 4 * (j + 2), pb, d);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double g = 2.0 * (E[0] * d[a][0] + E[1] * d[a][1] + E[2] * d[a][2]);
+        atomicAdd(s_kbar + 4 * j + 1 + a, g);
+      }
+    }
+    team_sync<TEAM>();
+    for (int it = lane; it < 3 * K; it += TEAM) {
+      const int j = 1 + it / 3, a = it % 3;
+      const double* kj = s_mom + 4 * (j + 2);
+      const double kn = sqrt(kj[1] * kj[1] + kj[2] * kj[2] + kj[3] * kj[3]);
+      const double g = s_kbar[4 * j + 1 + a] + s_kbar[4 * j] * kj[1 + a] / kn;
+      if (valid) p.grad[(pt * K + (j - 1)) * 3 + a] = g * p.coupling;
+    }
+    team_sync<TEAM>();
+  }
+}
+
+// Teams: one lane per polarisation pattern when the spin is summed (the
+// joins' layout), one warp for a fixed state.  Spin-summed k <= 5 and every
+// fixed-state k; none beyond (their subset currents and adjoints outgrow
+// shared memory).
+template <int K, bool SUMMED>
+KernelChoice pick_radj(bool mixed) {
+  constexpr int T = SUMMED ? (1 << (K + 1)) : 32;
+  if (mixed) return {qed_radj_kernel<K, SUMMED, float, T>, T};
+  return {qed_radj_kernel<K, SUMMED, double, T>, T};
+}
+
+KernelChoice radj_kernel(int k, bool summed, bool mixed) {
+  if (summed) {
+    switch (k) {
+      case 1: return pick_radj<1, true>(mixed);
+      case 2: return pick_radj<2, true>(mixed);
+      case 3: return pick_radj<3, true>(mixed);
+      case 4: return pick_radj<4, true>(mixed);
+      case 5: return pick_radj<5, true>(mixed);
+      default: return KernelChoice{nullptr, 0};
+    }
+  }
+  switch (k) {
+    case 1: return pick_radj<1, false>(mixed);
+    case 2: return pick_radj<2, false>(mixed);
+    case 3: return pick_radj<3, false>(mixed);
+    case 4: return pick_radj<4, false>(mixed);
+    case 5: return pick_radj<5, false>(mixed);
+    case 6: return pick_radj<6, false>(mixed);
+    case 7: return pick_radj<7, false>(mixed);
+    default: return KernelChoice{nullptr, 0};
+  }
+}
+
+}  // namespace qed

@@ -111,6 +111,32 @@ QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_p
   return A;
 }
 
+// Shared memory of one team of the rewritten-DAG adjoint (qed_radj.cu): the
+// forward team layout with ncur currents, then the currents' adjoints, the
+// amplitude seeds conj(M), FP64 accumulators of the propagator parameters
+// (5 per photon subset), of the polarisation parameters (3 per photon and
+// polarisation) and of the photon momenta, and per-lane accumulators of the
+// polarisation parameters in the working precision.
+struct RadjLayout {
+  TeamLayout fwd;
+  int adj, mbar, acc_s, acc_e, kbar, elane, bytes;
+};
+
+QED_HD RadjLayout radj_layout(int k, int real_size, int ncur, bool summed, int team) {
+  const int n = k + 1;
+  RadjLayout A;
+  A.fwd = team_layout(k, real_size, ncur);
+  int off = A.fwd.bytes;
+  A.adj = off;   off = align16(off + ncur * 8 * real_size);
+  A.mbar = off;  off = align16(off + (summed ? (1 << (n + 2)) : 1) * 2 * real_size);
+  A.acc_s = off; off = align16(off + (1 << n) * 5 * 8);
+  A.acc_e = off; off = align16(off + n * 2 * 3 * 8);
+  A.kbar = off;  off = align16(off + n * 4 * 8);
+  A.elane = off; off = align16(off + team * n * 2 * 3 * real_size);
+  A.bytes = off;
+  return A;
+}
+
 struct KParams {
   const double* mom;
   double* out;
@@ -160,6 +186,14 @@ struct KParams {
   int fix_set_off;
   int fix_rbase;
   int fix_ncur;
+  // adjoint on the rewritten DAG (qed_radj.cu): the photon subsets of every
+  // node, side 0 (column currents) then side 1 (row currents), level by
+  // level (side s, level l: entries radj_lev[s][l] .. radj_lev[s][l + 1] of
+  // radj_masks, l = 1..8), and radj_slot[(s << n) | mask], the node's first
+  // current (spin variant 0) or -1
+  const int* radj_masks;
+  int radj_lev[2][10];
+  const int* radj_slot;
   // tape plans (node-reduction sweep)
   const TapeInstr* tape;
   const int* tape_levels;          // instruction range of each level
