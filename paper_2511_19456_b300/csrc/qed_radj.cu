@@ -34,13 +34,16 @@
 //      of the node's own vertices;
 //   3. parameter terms -> photon momenta, as in qed_adj.cu.
 // The propagator terms of the lanes that share a node are summed by
-// shuffles, then added to FP64 accumulators by one lane; the polarisation
-// terms go to per-lane accumulators (no atomics), summed at the end.
+// shuffles and stored by one lane (each photon subset is the propagator of
+// one node); the polarisation terms go to per-lane accumulators, summed at
+// the end; no atomics.  In the mixed form the parameter chain to the
+// momenta runs on the FP32 pipe (compensated sums), the FP64 pipe (1/64 of
+// the FP32 rate on B300) being kept for the set-up and the final steps.
 #include <cuda_runtime.h>
 
 #include "qed_adjoint.cuh"
 #include "qed_plan.hpp"
-#include "qed_team.cuh"
+#include "qed_spec.cuh"
 
 namespace qed {
 
@@ -144,9 +147,10 @@ __device__ __forceinline__ void vertex_sum(const KParams& p, int side, unsigned 
 #pragma unroll
   for (int c = 0; c < 8; ++c) w[c] = (Real)0;
   int t = 0;
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    if (!((T >> j) & 1u)) continue;
+  // the photons of T in increasing order (all nodes of a round have as many)
+#pragma unroll 1
+  for (unsigned m = T; m; m &= m - 1u) {
+    const int j = __ffs((int)m) - 1;
     const int b = 1 + t++;
     Real x[8];
     int pol;
@@ -188,7 +192,11 @@ qed_radj_kernel(const KParams p) {
   Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
   Real* s_adj = reinterpret_cast<Real*>(base + A.adj);
   Real* s_mbar = reinterpret_cast<Real*>(base + A.mbar);
-  double* s_acc_s = reinterpret_cast<double*>(base + A.acc_s);
+  // propagator terms (Re s_mu, Re u) of each photon subset, in the working
+  // precision: every subset T with 0 < |T| < n is the propagator of exactly
+  // one node (column nodes have |T| < h, row nodes |T| >= h), whose lanes
+  // sum them and whose first lane stores them, so no accumulation is needed
+  Real* s_ps = reinterpret_cast<Real*>(base + A.acc_s);
   double* s_acc_e = reinterpret_cast<double*>(base + A.acc_e);
   double* s_kbar = reinterpret_cast<double*>(base + A.kbar);
   Real* s_el = reinterpret_cast<Real*>(base + A.elane) + lane * N * 6;   // this lane's polarisation terms
@@ -203,8 +211,14 @@ qed_radj_kernel(const KParams p) {
     const long long ptc = valid ? pt : p.n - 1;
 
     // ---- forward: external states, propagators, then the subset currents
-    point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin,
-                               reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
+    if constexpr (SUMMED && sizeof(Real) == 4 && K <= 4)
+      // FP64-light mixed set-up of the straight-line kernels (one lane per subset)
+      spec::setup_f32<K, TEAM>(p, lane, ptc, s_mom, reinterpret_cast<float*>(s_q), reinterpret_cast<float*>(s_eps),
+                               reinterpret_cast<float*>(s_spin), reinterpret_cast<double*>(base + L.w),
+                               reinterpret_cast<float*>(base + L.momf));
+    else
+      point_setup<K, Real, TEAM>(p, lane, ptc, s_mom, s_q, s_eps, s_spin,
+                                 reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
     for (int l = 1; l <= LMAX; ++l) {
       const int lg = SUMMED ? l + 1 : 0;
       const int cl = l <= H ? p.radj_lev[0][l + 1] - p.radj_lev[0][l] : 0;
@@ -285,7 +299,6 @@ qed_radj_kernel(const KParams p) {
       if (lane == 0) { s_mbar[0] = (Real)re; s_mbar[1] = (Real)(-im); }
     }
     if (lane == 0 && valid && p.out) p.out[pt] = m2 * p.coupling;
-    for (int i = lane; i < NSUB * 5; i += TEAM) s_acc_s[i] = 0.0;
     for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < N * 6; ++i) s_el[i] = (Real)0;
@@ -377,9 +390,10 @@ qed_radj_kernel(const KParams p) {
           } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) yb[c] = (Real)0;
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              if ((T >> j) & 1u) continue;
+            // the photons not in T: one parent each
+#pragma unroll 1
+            for (unsigned m = ALL & ~T; m; m &= m - 1u) {
+              const int j = __ffs((int)m) - 1;
               const unsigned Tp = T | (1u << j);
               const int bp = 1 + __popc(T & ((1u << j) - 1u));
               const int ps_slot = slot_of(p, N, side, Tp);
@@ -418,9 +432,9 @@ qed_radj_kernel(const KParams p) {
           // polarisation terms of the node's own vertices: -Re(wbar g^i x)
           // (column) or -Re(x g^i wbar) (row), per photon and polarisation
           int t = 0;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            if (!((T >> j) & 1u)) continue;
+#pragma unroll 1
+          for (unsigned m = T; m; m &= m - 1u) {
+            const int j = __ffs((int)m) - 1;
             const int b = 1 + t++;
             Real x[8];
             int pol;
@@ -440,65 +454,113 @@ qed_radj_kernel(const KParams p) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) ps[c] += __shfl_xor_sync(0xffffffffu, ps[c], off);
         if (ok && post && (v & (G - 1)) == 0) {
-          double* Ac = s_acc_s + post * 5;
 #pragma unroll
-          for (int c = 0; c < 5; ++c) atomicAdd(Ac + c, (double)ps[c]);
+          for (int c = 0; c < 5; ++c) s_ps[post * 5 + c] = ps[c];
         }
       }
       team_sync<TEAM>();
     }
 
-    // polarisation terms: the lanes' sums
+    // polarisation terms: the lanes' sums (FP64; in the mixed form a
+    // Kahan-compensated FP32 sum, which keeps the FP64 pipe free).  One
+    // fixed state uses one polarisation per photon.
     {
       const Real* el = reinterpret_cast<const Real*>(base + A.elane);
       for (int i = lane; i < N * 6; i += TEAM) {
-        double a = 0.0;
-        for (int ln = 0; ln < TEAM; ++ln) a += (double)el[ln * N * 6 + i];
-        s_acc_e[i] = a;
+        if constexpr (!SUMMED) {
+          const int j = i / 6, pol = (i / 3) & 1;
+          if (pol != (int)((p.fixed_pol_bits >> j) & 1u)) { s_acc_e[i] = 0.0; continue; }
+        }
+        if constexpr (sizeof(Real) == 8) {
+          double a = 0.0;
+          for (int ln = 0; ln < TEAM; ++ln) a += el[ln * N * 6 + i];
+          s_acc_e[i] = a;
+        } else {
+          float a = 0.f, c = 0.f;
+          for (int ln = 0; ln < TEAM; ++ln) {
+            const float y = __fsub_rn(el[ln * N * 6 + i], c);
+            const float t = __fadd_rn(a, y);
+            c = __fsub_rn(__fsub_rn(t, a), y);
+            a = t;
+          }
+          s_acc_e[i] = (double)a - (double)c;
+        }
       }
     }
     team_sync<TEAM>();
 
-    // ---- 3. parameters -> outgoing photon momenta (FP64)
+    // ---- 3. parameters -> outgoing photon momenta
+    // df/dQ_T^mu = 2 eta_mu (s_mu - 2 Q^mu u) / D, in place of the subset's
+    // terms.  FP64: Q_T and D_T formed again in FP64.  Mixed: from the FP32
+    // propagator entries of the set-up, Q^mu / D and 1 / D = (A - B) / 2m
+    // with A, B = (Q0 +- m) / D (relative error about u32 Q0 / m, far below
+    // the FP32 terms' own).
 #pragma unroll 1
     for (int mask = lane; mask < NSUB; mask += TEAM) {
       if (mask == 0 || mask == (int)ALL) continue;
-      double q0 = s_mom[0], q1 = s_mom[1], q2 = s_mom[2], q3 = s_mom[3];
-      for (int j = 0; j < N; ++j) {
-        if (!(mask & (1 << j))) continue;
-        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
-        if (j == 0) { q0 += kj[0]; q1 += kj[1]; q2 += kj[2]; q3 += kj[3]; }
-        else        { q0 -= kj[0]; q1 -= kj[1]; q2 -= kj[2]; q3 -= kj[3]; }
-      }
-      double D = __dmul_rn(q0, q0);
-      D = __dsub_rn(D, __dmul_rn(q1, q1));
-      D = __dsub_rn(D, __dmul_rn(q2, q2));
-      D = __dsub_rn(D, __dmul_rn(q3, q3));
-      D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
-      // df/dQ_T^mu = 2 eta_mu (s_mu - 2 Q^mu u) / D, in place of the subset's accumulator
-      double* Ac = s_acc_s + mask * 5;
-      const double Q[4] = {q0, q1, q2, q3};
-      const double two_inv_d = 2.0 / D;
-      double qb[4];
+      Real* Ac = s_ps + mask * 5;
+      if constexpr (sizeof(Real) == 8) {
+        double q0 = s_mom[0], q1 = s_mom[1], q2 = s_mom[2], q3 = s_mom[3];
+        for (int j = 0; j < N; ++j) {
+          if (!(mask & (1 << j))) continue;
+          const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
+          if (j == 0) { q0 += kj[0]; q1 += kj[1]; q2 += kj[2]; q3 += kj[3]; }
+          else        { q0 -= kj[0]; q1 -= kj[1]; q2 -= kj[2]; q3 -= kj[3]; }
+        }
+        double D = __dmul_rn(q0, q0);
+        D = __dsub_rn(D, __dmul_rn(q1, q1));
+        D = __dsub_rn(D, __dmul_rn(q2, q2));
+        D = __dsub_rn(D, __dmul_rn(q3, q3));
+        D = __dsub_rn(D, __dmul_rn(p.mass, p.mass));
+        const double Q[4] = {q0, q1, q2, q3};
+        const double two_inv_d = 2.0 / D;
+        double qb[4];
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        const double eta = mu == 0 ? 1.0 : -1.0;
-        qb[mu] = eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) * two_inv_d;
-      }
+        for (int mu = 0; mu < 4; ++mu) {
+          const double eta = mu == 0 ? 1.0 : -1.0;
+          qb[mu] = eta * (Ac[mu] - 2.0 * Q[mu] * Ac[4]) * two_inv_d;
+        }
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) Ac[mu] = qb[mu];
+        for (int mu = 0; mu < 4; ++mu) Ac[mu] = qb[mu];
+      } else {
+        const float* P = reinterpret_cast<const float*>(s_q) + mask * 5;
+        const float inv_d = __fdiv_rn(__fsub_rn(P[0], P[1]), 2.0f * (float)p.mass);
+        const float qd[4] = {0.5f * __fadd_rn(P[0], P[1]), P[2], P[3], P[4]};   // Q^mu / D
+        const float u2 = 2.0f * Ac[4];
+        float qb[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          const float t = __fmaf_rn(-u2, qd[mu], Ac[mu] * inv_d);
+          qb[mu] = mu == 0 ? 2.0f * t : -2.0f * t;
+        }
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) Ac[mu] = qb[mu];
+      }
     }
     team_sync<TEAM>();
     // Q_T = p + k_0 - sum_{j in T, j >= 1} k_j: df/dk_j^mu = -sum over the
-    // subsets T that contain j of df/dQ_T^mu, one lane per (j, mu)
+    // subsets T that contain j of df/dQ_T^mu, one lane per (j, mu); in the
+    // mixed form summed in float-float (TwoSum)
     for (int it = lane; it < K * 4; it += TEAM) {
       const int j = 1 + (it >> 2), mu = it & 3;
       const int lo = (1 << j) - 1;
-      double a = 0.0;
+      if constexpr (sizeof(Real) == 8) {
+        double a = 0.0;
 #pragma unroll 1
-      for (int r = 0; r < (1 << (N - 1)) - 1; ++r)   // r = 2^(n-1) - 1 would be the full set
-        a += s_acc_s[(((r >> j) << (j + 1)) | (1 << j) | (r & lo)) * 5 + mu];
-      s_kbar[4 * j + mu] = -a;
+        for (int r = 0; r < (1 << (N - 1)) - 1; ++r)   // r = 2^(n-1) - 1 would be the full set
+          a += s_ps[(((r >> j) << (j + 1)) | (1 << j) | (r & lo)) * 5 + mu];
+        s_kbar[4 * j + mu] = -a;
+      } else {
+        float hi = 0.f, lo_ = 0.f;
+#pragma unroll 1
+        for (int r = 0; r < (1 << (N - 1)) - 1; ++r) {
+          float sum, err;
+          two_sum_f(hi, s_ps[(((r >> j) << (j + 1)) | (1 << j) | (r & lo)) * 5 + mu], sum, err);
+          hi = sum;
+          lo_ = __fadd_rn(lo_, err);
+        }
+        s_kbar[4 * j + mu] = -((double)hi + (double)lo_);
+      }
     }
     team_sync<TEAM>();
     for (int it = lane; it < 2 * N; it += TEAM) {
