@@ -56,6 +56,7 @@ void free_plan(qed_plan_s* p) {
   cudaFree(p->d_fix_items);
   cudaFree(p->d_radj_masks);
   cudaFree(p->d_radj_slot);
+  cudaFree(p->d_radj_aslot);
   cudaFree(p->d_stage);
   if (p->ev_scratch) cudaEventDestroy(p->ev_scratch);
   for (int i = 0; i < 2; ++i) {
@@ -201,9 +202,9 @@ qed_status setup_radj(qed_plan_s* P, bool mixed, int dev_smem, int sms, bool* do
   const KernelChoice kc = radj_kernel(P->k, P->summed, mixed);
   if (!kc.fn) return QED_OK;
   const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
-  std::vector<int> masks, slot(2u << n, -1);
+  std::vector<int> masks, slot(2u << n, -1), aslot(2u << n, -1);
   int lev[2][10] = {{0}};
-  int next = 0;
+  int next = 0, anext = 0;
   for (int side = 0; side < 2; ++side) {
     const int top = side == 0 ? h : r;
     for (int l = 1; l <= 9; ++l) {
@@ -212,16 +213,23 @@ qed_status setup_radj(qed_plan_s* P, bool mixed, int dev_smem, int sms, bool* do
       for (int T = 1; T < (1 << n); ++T) {
         if (__builtin_popcount(T) != l) continue;
         masks.push_back(T);
+        const int nv = P->summed ? (2 << l) : 1;
         slot[(side << n) | T] = next;
-        next += P->summed ? (2 << l) : 1;
+        next += nv;
+        if (side == 1 || l < h) {   // a column leaf's adjoint takes its current's place
+          aslot[(side << n) | T] = anext;
+          anext += nv;
+        }
       }
     }
   }
   const int team = kc.team, block = std::max(team, 32);
-  const size_t smem = (size_t)(block / team) * radj_layout(k, mixed ? 4 : 8, next, P->summed, team).bytes;
+  const size_t smem =
+      (size_t)(block / team) * radj_layout(k, mixed ? 4 : 8, next, anext, P->summed, team).bytes;
   if (smem > (size_t)dev_smem) return QED_OK;
   cudaError_t e = upload(&P->d_radj_masks, masks);
   if (e == cudaSuccess) e = upload(&P->d_radj_slot, slot);
+  if (e == cudaSuccess) e = upload(&P->d_radj_aslot, aslot);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)kc.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
@@ -230,6 +238,7 @@ qed_status setup_radj(qed_plan_s* P, bool mixed, int dev_smem, int sms, bool* do
   if (per_sm < 1) return QED_OK;
   std::memcpy(P->radj_lev, lev, sizeof(lev));
   P->radj_ncur = next;
+  P->radj_nadj = anext;
   P->radj = true;
   P->kc_adj = kc;
   P->block_adj = block;
@@ -1019,6 +1028,8 @@ qed_status launch_grad(qed_plan_t P, const double* d_momenta, long long n, doubl
   if (P->radj) {
     kp.radj_masks = P->d_radj_masks;
     kp.radj_slot = P->d_radj_slot;
+    kp.radj_aslot = P->d_radj_aslot;
+    kp.radj_nadj = P->radj_nadj;
     std::memcpy(kp.radj_lev, P->radj_lev, sizeof(kp.radj_lev));
     kp.ncur = P->radj_ncur;
   }

@@ -112,8 +112,9 @@ struct qed_plan_s {
   bool radj = false;
   int* d_radj_masks = nullptr;
   int* d_radj_slot = nullptr;
+  int* d_radj_aslot = nullptr;
   int radj_lev[2][10] = {{0}};
-  int radj_ncur = 0;
+  int radj_ncur = 0, radj_nadj = 0;
   int n_part = 0;
   int device = 0;
   // staging for qed_eval_host (one call at a time per plan: stage_lock)

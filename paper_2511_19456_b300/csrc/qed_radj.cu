@@ -109,6 +109,42 @@ __device__ __forceinline__ unsigned pdep_n(unsigned x, unsigned mask) {
 __device__ __forceinline__ int slot_of(const KParams& p, int n, int side, unsigned mask) {
   return __ldg(p.radj_slot + (side << n) + (int)mask);
 }
+__device__ __forceinline__ int aslot_of(const KParams& p, int n, int side, unsigned mask) {
+  return __ldg(p.radj_aslot + (side << n) + (int)mask);
+}
+
+// Currents in planes of 16 bytes: entry i of a buffer of n entries keeps its
+// reals [q * P, (q + 1) * P) at plane q (P = 16 / sizeof(Real)), so that the
+// lanes of a round, which mostly take consecutive entries, read and write
+// consecutive 16-byte words (no shared-memory bank conflicts).
+template <typename Real>
+struct Planes {
+  static constexpr int P = 16 / (int)sizeof(Real), NQ = 8 / P;
+  Real* base;
+  int n;
+  __device__ __forceinline__ void ld(int i, Real x[8]) const {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if constexpr (P == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(base + ((size_t)q * n + i) * P);
+        x[4 * q] = a.x; x[4 * q + 1] = a.y; x[4 * q + 2] = a.z; x[4 * q + 3] = a.w;
+      } else {
+        const double2 a = *reinterpret_cast<const double2*>(base + ((size_t)q * n + i) * P);
+        x[2 * q] = a.x; x[2 * q + 1] = a.y;
+      }
+    }
+  }
+  __device__ __forceinline__ void st(int i, const Real x[8]) const {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if constexpr (P == 4)
+        *reinterpret_cast<float4*>(base + ((size_t)q * n + i) * P) =
+            make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+      else
+        *reinterpret_cast<double2*>(base + ((size_t)q * n + i) * P) = make_double2(x[2 * q], x[2 * q + 1]);
+    }
+  }
+};
 
 // Spin variant of a node without / with the polarisation bit b (bit 0 is the
 // electron helicity, bit 1 + r the polarisation of the set's photon of rank r).
@@ -122,7 +158,7 @@ __device__ __forceinline__ int ins_bit(int v, int b, int pol) {
 // returns j's polarisation in this variant.
 template <int N, bool SUMMED, typename Real>
 __device__ __forceinline__ void vertex_input(const KParams& p, int side, unsigned T, int j, int b, int v,
-                                             const Real* s_spin, const Real* s_cur, Real x[8], int& pol) {
+                                             const Real* s_spin, const Planes<Real>& cur, Real x[8], int& pol) {
   int vp;
   if constexpr (SUMMED) {
     pol = (v >> b) & 1;
@@ -136,14 +172,14 @@ __device__ __forceinline__ void vertex_input(const KParams& p, int side, unsigne
     const int e = SUMMED ? vp : (side == 0 ? p.fixed_sin : p.fixed_sout);
     load8(s_spin + (side * 2 + e) * 8, x);
   } else {
-    load_cur(s_cur, slot_of(p, N, side, Tm), 0, vp, x);
+    cur.ld(slot_of(p, N, side, Tm) + vp, x);
   }
 }
 
 // The node's sum of vertex terms before its propagator: J_T (column) or I_U (row).
 template <int N, bool SUMMED, typename Real>
 __device__ __forceinline__ void vertex_sum(const KParams& p, int side, unsigned T, int v, const Real* s_eps,
-                                           const Real* s_spin, const Real* s_cur, Real w[8]) {
+                                           const Real* s_spin, const Planes<Real>& cur, Real w[8]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) w[c] = (Real)0;
   int t = 0;
@@ -154,7 +190,7 @@ __device__ __forceinline__ void vertex_sum(const KParams& p, int side, unsigned 
     const int b = 1 + t++;
     Real x[8];
     int pol;
-    vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, s_cur, x, pol);
+    vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, cur, x, pol);
     Real ev[3];
     load_e3(s_eps + (j * 2 + pol) * 4, ev);
     if (side == 0) vacc_col(ev, x, w); else vacc_row(ev, x, w);
@@ -178,7 +214,7 @@ qed_radj_kernel(const KParams p) {
   static_assert(!SUMMED || TEAM == (1 << N), "one lane per polarisation pattern");
 
   extern __shared__ __align__(16) unsigned char smem[];
-  const RadjLayout A = radj_layout(K, (int)sizeof(Real), p.ncur, SUMMED, TEAM);
+  const RadjLayout A = radj_layout(K, (int)sizeof(Real), p.ncur, p.radj_nadj, SUMMED, TEAM);
   const TeamLayout& L = A.fwd;
   const int lane = threadIdx.x & (TEAM - 1);
   const int team = threadIdx.x / TEAM;
@@ -189,8 +225,10 @@ qed_radj_kernel(const KParams p) {
   Real* s_eps = reinterpret_cast<Real*>(base + L.eps);
   Real* s_spin = reinterpret_cast<Real*>(base + L.spin);
   double* s_red = reinterpret_cast<double*>(base + L.red);
-  Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
-  Real* s_adj = reinterpret_cast<Real*>(base + A.adj);
+  // forward currents, and the adjoints of every node but the column leaves,
+  // whose adjoints replace their currents once the joins are transposed
+  const Planes<Real> cur{reinterpret_cast<Real*>(base + L.cur), p.ncur};
+  const Planes<Real> adj{reinterpret_cast<Real*>(base + A.adj), p.radj_nadj};
   Real* s_mbar = reinterpret_cast<Real*>(base + A.mbar);
   // propagator terms (Re s_mu, Re u) of each photon subset, in the working
   // precision: every subset T with 0 < |T| < n is the propagator of exactly
@@ -230,15 +268,15 @@ qed_radj_kernel(const KParams p) {
         const unsigned T = (unsigned)__ldg(masks + p.radj_lev[side][l] + (q >> lg));
         const int v = q & ((1 << lg) - 1);
         Real w[8];
-        vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, s_cur, w);
+        vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, cur, w);
         const unsigned post = side == 0 ? (l < H ? T : 0u) : (ALL & ~T);
-        const int dst = slot_of(p, N, side, T);
+        const int dst = slot_of(p, N, side, T) + v;
         if (post) {
           Real z[8];
           if (side == 0) prop_col(s_q + post * 5, w, z); else prop_row(s_q + post * 5, w, z);
-          store_cur(s_cur, dst, 0, v, z);
+          cur.st(dst, z);
         } else {
-          store_cur(s_cur, dst, 0, v, w);
+          cur.st(dst, w);
         }
       }
       team_sync<TEAM>();
@@ -255,8 +293,8 @@ qed_radj_kernel(const KParams p) {
         Real lc[2][8], rw[2][8];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          load_cur(s_cur, ls, 0, vl + e, lc[e]);
-          load_cur(s_cur, rs, 0, vr + e, rw[e]);
+          cur.ld(ls + vl + e, lc[e]);
+          cur.ld(rs + vr + e, rw[e]);
         }
 #pragma unroll
         for (int si = 0; si < 2; ++si)
@@ -271,8 +309,8 @@ qed_radj_kernel(const KParams p) {
       for (int s = lane; s < nsets; s += TEAM) {
         const unsigned S = (unsigned)__ldg(set_masks + s);
         Real lc[8], rw[8];
-        load_cur(s_cur, slot_of(p, N, 0, S), 0, 0, lc);
-        load_cur(s_cur, slot_of(p, N, 1, ALL & ~S), 0, 0, rw);
+        cur.ld(slot_of(p, N, 0, S), lc);
+        cur.ld(slot_of(p, N, 1, ALL & ~S), rw);
         Real yr = (Real)0, yi = (Real)0;
         dot_acc(rw, lc, yr, yi);
         acc[0].add(yr, yi);
@@ -300,62 +338,69 @@ qed_radj_kernel(const KParams p) {
     }
     if (lane == 0 && valid && p.out) p.out[pt] = m2 * p.coupling;
     for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
-#pragma unroll
-    for (int i = 0; i < N * 6; ++i) s_el[i] = (Real)0;
     team_sync<TEAM>();
 
-    // ---- 1. transposed joins, into the leaves' adjoint slots
+    // ---- 1. transposed joins.  First the row leaves' adjoints (they read
+    // the column leaves), then the column leaves' adjoints, which replace
+    // their currents (they read only the row leaves)
     {
       constexpr int NVL = SUMMED ? 2 << H : 1, NVR = SUMMED ? 2 << R : 1;
-      const int totl = nsets * NVL, tot = nsets * (NVL + NVR);
-      for (int it = lane; it < tot; it += TEAM) {
-        const bool left = it < totl;
-        const int q = left ? it : it - totl;
-        const int s = left ? q / NVL : q / NVR;
-        const int v = left ? q % NVL : q % NVR;
-        const unsigned S = (unsigned)__ldg(set_masks + s), Sc = ALL & ~S;
-        // the other side of the join: the row leaf of S^c for a left item,
-        // the column leaf of S for a right item
-        const unsigned mine = left ? S : Sc, other = left ? Sc : S;
-        const int os = slot_of(p, N, left ? 1 : 0, other);
-        Real o[8];
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool left = pass == 1;
+        const int nvm = left ? NVL : NVR;
+        const int tot = nsets * nvm;
+        for (int it = lane; it < tot; it += TEAM) {
+          const int s = it / nvm, v = it % nvm;
+          const unsigned S = (unsigned)__ldg(set_masks + s), Sc = ALL & ~S;
+          // the other side of the join: the row leaf of S^c for a column
+          // leaf's adjoint, the column leaf of S for a row leaf's
+          const unsigned mine = left ? S : Sc, other = left ? Sc : S;
+          const int os = slot_of(p, N, left ? 1 : 0, other);
+          Real o[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) o[c] = (Real)0;
-        if constexpr (SUMMED) {
-          const unsigned cm = pdep_n<N>((unsigned)v >> 1, mine);
-          const int e_mine = v & 1;
-          constexpr int NOTHER_L = 1 << R, NOTHER_R = 1 << H;
-          const int nq = left ? NOTHER_L : NOTHER_R;
-          unsigned co = 0;   // submasks of `other` in increasing order: pdep(q, other)
-          for (int qq = 0; qq < nq; ++qq) {
+          for (int c = 0; c < 8; ++c) o[c] = (Real)0;
+          if constexpr (SUMMED) {
+            const unsigned cm = pdep_n<N>((unsigned)v >> 1, mine);
+            const int e_mine = v & 1;
+            const int nq = left ? (1 << R) : (1 << H);
+            unsigned co = 0;   // submasks of `other` in increasing order: pdep(q, other)
+#pragma unroll 1
+            for (int qq = 0; qq < nq; ++qq) {
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int si = left ? e_mine : e, so = left ? e : e_mine;
-              const int lam = si | (so << 1) | (int)((cm | co) << 2);
-              const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
-              Real x[8];
-              load_cur(s_cur, os, 0, (qq << 1) | e, x);
+              for (int e = 0; e < 2; ++e) {
+                const int si = left ? e_mine : e, so = left ? e : e_mine;
+                const int lam = si | (so << 1) | (int)((cm | co) << 2);
+                const Real mr = s_mbar[2 * lam], mi = s_mbar[2 * lam + 1];
+                Real x[8];
+                cur.ld(os + ((qq << 1) | e), x);
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                o[2 * c] = fma(mr, x[2 * c], fma(-mi, x[2 * c + 1], o[2 * c]));
-                o[2 * c + 1] = fma(mr, x[2 * c + 1], fma(mi, x[2 * c], o[2 * c + 1]));
+                for (int c = 0; c < 4; ++c) {
+                  o[2 * c] = fma(mr, x[2 * c], fma(-mi, x[2 * c + 1], o[2 * c]));
+                  o[2 * c + 1] = fma(mr, x[2 * c + 1], fma(mi, x[2 * c], o[2 * c + 1]));
+                }
               }
+              co = ((co | ~other) + 1u) & other;
             }
-            co = ((co | ~other) + 1u) & other;
-          }
-        } else {
-          const Real mr = s_mbar[0], mi = s_mbar[1];
-          Real x[8];
-          load_cur(s_cur, os, 0, 0, x);
+          } else {
+            const Real mr = s_mbar[0], mi = s_mbar[1];
+            Real x[8];
+            cur.ld(os, x);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            o[2 * c] = mr * x[2 * c] - mi * x[2 * c + 1];
-            o[2 * c + 1] = mr * x[2 * c + 1] + mi * x[2 * c];
+            for (int c = 0; c < 4; ++c) {
+              o[2 * c] = mr * x[2 * c] - mi * x[2 * c + 1];
+              o[2 * c + 1] = mr * x[2 * c + 1] + mi * x[2 * c];
+            }
           }
+          if (left) cur.st(slot_of(p, N, 0, mine) + v, o);
+          else adj.st(aslot_of(p, N, 1, mine) + v, o);
         }
-        store_cur(s_adj, slot_of(p, N, left ? 0 : 1, mine), 0, v, o);
+        team_sync<TEAM>();
       }
     }
+    // the seeds are read: their space takes the per-lane polarisation terms
+#pragma unroll
+    for (int i = 0; i < N * 6; ++i) s_el[i] = (Real)0;
     team_sync<TEAM>();
 
     // ---- 2. the levels, deepest first
@@ -382,11 +427,15 @@ qed_radj_kernel(const KParams p) {
         for (int c = 0; c < 5; ++c) ps[c] = (Real)0;
         if (ok) {
           const int my = slot_of(p, N, side, T);
-          // the node's output adjoint ybar: from the joins (leaves) or
-          // gathered from the parents' pre-propagator adjoints
+          const int amy = aslot_of(p, N, side, T);
+          // the node's output adjoint ybar: from the joins (leaves; a column
+          // leaf's in place of its current) or gathered from the parents'
+          // pre-propagator adjoints
           Real yb[8];
-          if (l == (side ? R : H)) {
-            load_cur(s_adj, my, 0, v, yb);
+          if (leaf_l) {
+            cur.ld(my + v, yb);
+          } else if (side == 1 && l == R) {
+            adj.ld(amy + v, yb);
           } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) yb[c] = (Real)0;
@@ -396,13 +445,15 @@ qed_radj_kernel(const KParams p) {
               const int j = __ffs((int)m) - 1;
               const unsigned Tp = T | (1u << j);
               const int bp = 1 + __popc(T & ((1u << j) - 1u));
-              const int ps_slot = slot_of(p, N, side, Tp);
+              // a column leaf keeps its adjoint in its current's place
+              const bool in_cur = side == 0 && l + 1 == H;
+              const int ps_slot = in_cur ? slot_of(p, N, 0, Tp) : aslot_of(p, N, side, Tp);
 #pragma unroll
               for (int pol = 0; pol < (SUMMED ? 2 : 1); ++pol) {
                 const int pl = SUMMED ? pol : (int)((p.fixed_pol_bits >> j) & 1u);
                 const int vpar = SUMMED ? ins_bit(v, bp, pol) : 0;
                 Real wb[8], ev[3];
-                load_cur(s_adj, ps_slot, 0, vpar, wb);
+                if (in_cur) cur.ld(ps_slot + vpar, wb); else adj.ld(ps_slot + vpar, wb);
                 load_e3(s_eps + (j * 2 + pl) * 4, ev);
                 // transposed vertex: column x -> eps/ x gives xbar = wbar eps/
                 if (side == 0) vacc_row(ev, wb, yb); else vacc_col(ev, wb, yb);
@@ -416,8 +467,8 @@ qed_radj_kernel(const KParams p) {
             const Real* P = s_q + post * 5;
             if (side == 0) prop_row(P, yb, wb); else prop_col(P, yb, wb);
             Real w[8], y[8];
-            vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, s_cur, w);
-            load_cur(s_cur, my, 0, v, y);
+            vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, cur, w);
+            cur.ld(my + v, y);
             if (side == 0) {
               ps[0] = bil_s0(yb, w); ps[1] = bil_s1(yb, w); ps[2] = bil_s2(yb, w); ps[3] = bil_s3(yb, w);
               ps[4] = bil_u(yb, y);
@@ -438,7 +489,7 @@ qed_radj_kernel(const KParams p) {
             const int b = 1 + t++;
             Real x[8];
             int pol;
-            vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, s_cur, x, pol);
+            vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, cur, x, pol);
             Real* E = s_el + j * 6 + pol * 3;
             if (side == 0) {
               E[0] -= bil_s1(wb, x); E[1] -= bil_s2(wb, x); E[2] -= bil_s3(wb, x);
@@ -446,7 +497,7 @@ qed_radj_kernel(const KParams p) {
               E[0] -= bil_s1(x, wb); E[1] -= bil_s2(x, wb); E[2] -= bil_s3(x, wb);
             }
           }
-          if (!leaf_l) store_cur(s_adj, my, 0, v, wb);
+          if (!leaf_l) adj.st(amy + v, wb);
         }
         // the propagator terms of one node's variants: summed over its lanes,
         // added to the FP64 accumulators by the first

@@ -112,27 +112,32 @@ QED_HD AdjLayout adj_layout(int k, int real_size, int ncur, bool summed, int n_p
 }
 
 // Shared memory of one team of the rewritten-DAG adjoint (qed_radj.cu): the
-// forward team layout with ncur currents, then the currents' adjoints, the
-// amplitude seeds conj(M), FP64 accumulators of the propagator parameters
-// (5 per photon subset), of the polarisation parameters (3 per photon and
-// polarisation) and of the photon momenta, and per-lane accumulators of the
-// polarisation parameters in the working precision.
+// forward team layout with ncur currents, then nadj current adjoints, the
+// amplitude seeds conj(M) or (later) per-lane accumulators of the
+// polarisation parameters in the working precision, the propagator
+// parameters of every photon subset (5, working precision), and FP64
+// accumulators of the polarisation parameters (3 per photon and
+// polarisation) and of the photon momenta.
 struct RadjLayout {
   TeamLayout fwd;
   int adj, mbar, acc_s, acc_e, kbar, elane, bytes;
 };
 
-QED_HD RadjLayout radj_layout(int k, int real_size, int ncur, bool summed, int team) {
+QED_HD RadjLayout radj_layout(int k, int real_size, int ncur, int nadj, bool summed, int team) {
   const int n = k + 1;
   RadjLayout A;
   A.fwd = team_layout(k, real_size, ncur);
   int off = A.fwd.bytes;
-  A.adj = off;   off = align16(off + ncur * 8 * real_size);
-  A.mbar = off;  off = align16(off + (summed ? (1 << (n + 2)) : 1) * 2 * real_size);
-  A.acc_s = off; off = align16(off + (1 << n) * 5 * 8);
+  A.adj = off;   off = align16(off + nadj * 8 * real_size);
+  // the seeds (needed until the joins are transposed) and the per-lane
+  // polarisation terms (needed after) share their space
+  const int mbar_bytes = (summed ? (1 << (n + 2)) : 1) * 2 * real_size;
+  const int elane_bytes = team * n * 2 * 3 * real_size;
+  A.mbar = A.elane = off;
+  off = align16(off + (mbar_bytes > elane_bytes ? mbar_bytes : elane_bytes));
+  A.acc_s = off; off = align16(off + (1 << n) * 5 * real_size);
   A.acc_e = off; off = align16(off + n * 2 * 3 * 8);
   A.kbar = off;  off = align16(off + n * 4 * 8);
-  A.elane = off; off = align16(off + team * n * 2 * 3 * real_size);
   A.bytes = off;
   return A;
 }
@@ -194,6 +199,10 @@ struct KParams {
   const int* radj_masks;
   int radj_lev[2][10];
   const int* radj_slot;
+  // ... radj_aslot: the node's first adjoint of radj_nadj (-1 for the
+  // column leaves, whose adjoints take their currents' place)
+  const int* radj_aslot;
+  int radj_nadj;
   // tape plans (node-reduction sweep)
   const TapeInstr* tape;
   const int* tape_levels;          // instruction range of each level
