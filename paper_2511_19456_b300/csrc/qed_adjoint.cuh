@@ -54,31 +54,33 @@ __device__ __forceinline__ Real bil_u(const Real* a, const Real* b) {
   return fre(a, 3, b, 3, one, fre(a, 2, b, 2, one, fre(a, 1, b, 1, one, fre(a, 0, b, 0, one, (Real)0))));
 }
 
-// d eps_pol / d k_a (a = x, y, z) for the real linear polarisations; zero on
-// the z axis, where the basis is fixed by convention.
-__device__ __forceinline__ void dpol(const double* k, int pbit, double d[3][3]) {
-  const double kx = k[1], ky = k[2], kz = k[3];
-  const double kt2 = kx * kx + ky * ky;
+// d eps_pol / d k_a (a = x, y, z) for the real linear polarisations, in
+// precision T (the momentum is FP64); zero on the z axis, where the basis is
+// fixed by convention.
+template <typename T>
+__device__ __forceinline__ void dpol(const double* k, int pbit, T d[3][3]) {
+  const T kx = (T)k[1], ky = (T)k[2], kz = (T)k[3];
+  const T kt2 = kx * kx + ky * ky;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[a][i] = 0.0;
-  if (kt2 == 0.0) return;
-  const double kt = sqrt(kt2);
+    for (int i = 0; i < 3; ++i) d[a][i] = (T)0;
+  if (kt2 == (T)0) return;
+  const T kt = sqrt(kt2);
   if (pbit) {
     // eps_2 = (-ky, kx, 0) / kT
-    const double c = 1.0 / (kt2 * kt);
+    const T c = (T)1 / (kt2 * kt);
     d[0][0] = kx * ky * c; d[0][1] = ky * ky * c;
     d[1][0] = -kx * kx * c; d[1][1] = -kx * ky * c;
     return;
   }
   // eps_1 = g (kx kz, ky kz, -kT^2), g = 1 / (K kT)
-  const double K2 = kt2 + kz * kz;
-  const double K = sqrt(K2);
-  const double g = 1.0 / (K * kt);
-  const double num[3] = {kx * kz, ky * kz, -kt2};
-  const double dg[3] = {-g * (kx / K2 + kx / kt2), -g * (ky / K2 + ky / kt2), -g * kz / K2};
-  const double dn[3][3] = {{kz, 0.0, -2.0 * kx}, {0.0, kz, -2.0 * ky}, {kx, ky, 0.0}};
+  const T K2 = kt2 + kz * kz;
+  const T K = sqrt(K2);
+  const T g = (T)1 / (K * kt);
+  const T num[3] = {kx * kz, ky * kz, -kt2};
+  const T dg[3] = {-g * (kx / K2 + kx / kt2), -g * (ky / K2 + ky / kt2), -g * kz / K2};
+  const T dn[3][3] = {{kz, (T)0, (T)-2 * kx}, {(T)0, kz, (T)-2 * ky}, {kx, ky, (T)0}};
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll

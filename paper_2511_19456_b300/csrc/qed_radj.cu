@@ -330,11 +330,23 @@ qed_radj_kernel(const KParams p) {
         s_mbar[2 * lam + 1] = (Real)(-im);
       }
       m2 = team_sum<TEAM>(part, s_red);
-    } else {
+    } else if constexpr (sizeof(Real) == 8) {
       const double re = team_sum<TEAM>(acc[0].vre(), s_red);
       const double im = team_sum<TEAM>(acc[0].vim(), s_red);
       m2 = re * re + im * im;
       if (lane == 0) { s_mbar[0] = (Real)re; s_mbar[1] = (Real)(-im); }
+    } else {
+      // the lanes' compensated sums in float-float (FP32 pipe), squared in FP64
+      float rh = acc[0].re, rl = -acc[0].cre, ih = acc[0].im, il = -acc[0].cim;
+      team_sum_ff<TEAM>(rh, rl, lane, reinterpret_cast<float*>(s_red));
+      team_sum_ff<TEAM>(ih, il, lane, reinterpret_cast<float*>(s_red) + 8);
+      m2 = 0.0;
+      if (lane == 0) {
+        const double re = (double)rh + (double)rl, im = (double)ih + (double)il;
+        m2 = re * re + im * im;
+        s_mbar[0] = (Real)re;
+        s_mbar[1] = (Real)(-im);
+      }
     }
     if (lane == 0 && valid && p.out) p.out[pt] = m2 * p.coupling;
     for (int i = lane; i < N * 4; i += TEAM) s_kbar[i] = 0.0;
@@ -614,17 +626,20 @@ qed_radj_kernel(const KParams p) {
       }
     }
     team_sync<TEAM>();
-    for (int it = lane; it < 2 * N; it += TEAM) {
-      const int j = it >> 1, pb = it & 1;
-      if (j == 0) continue;
-      const double* E = s_acc_e + (j * 2 + pb) * 3;
-      double d[3][3];
-      dpol(s_mom + 4 * (j + 2), pb, d);
+    // polarisation terms through d eps / d k_j (in the working precision),
+    // one lane per (photon, component) over both polarisations
+    for (int it = lane; it < 3 * K; it += TEAM) {
+      const int j = 1 + it / 3, a = it % 3;
+      double g = 0.0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double g = 2.0 * (E[0] * d[a][0] + E[1] * d[a][1] + E[2] * d[a][2]);
-        atomicAdd(s_kbar + 4 * j + 1 + a, g);
+      for (int pb = 0; pb < 2; ++pb) {
+        const double* E = s_acc_e + (j * 2 + pb) * 3;
+        Real d[3][3];
+        dpol<Real>(s_mom + 4 * (j + 2), pb, d);
+        g += 2.0 * ((double)E[0] * (double)d[a][0] + (double)E[1] * (double)d[a][1] +
+                    (double)E[2] * (double)d[a][2]);
       }
+      s_kbar[4 * j + 1 + a] += g;
     }
     team_sync<TEAM>();
     for (int it = lane; it < 3 * K; it += TEAM) {

@@ -36,6 +36,40 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
   return v;
 }
 
+// Float-float addition (hi, lo) += (bh, bl): Knuth's TwoSum of the high
+// parts, the low parts added to its error, then renormalised (Dekker's
+// Fast2Sum), about 2^-48 relative; all on the FP32 pipe.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum_f(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// The team's sum of one float-float value per lane (a compensated diagram
+// sum re - c as the pair (re, -c)), returned to lane 0 of the team: warp
+// shuffles, then through shared memory across the warps of a team of W > 1.
+// Every lane of the team must call it.
+template <int TEAM, int W = (TEAM > 32 ? TEAM / 32 : 1)>
+__device__ __forceinline__ void team_sum_ff(float& hi, float& lo, int lane, float* red) {
+  constexpr int WL = TEAM / W;
+#pragma unroll
+  for (int off = WL / 2; off > 0; off >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, off);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, off);
+    ff_add(hi, lo, bh, bl);
+  }
+  if constexpr (W > 1) {
+    const int wi = lane / WL;
+    __syncthreads();
+    if (lane % WL == 0) { red[2 * wi] = hi; red[2 * wi + 1] = lo; }
+    __syncthreads();
+    if (lane == 0)
+      for (int w = 1; w < W; ++w) ff_add(hi, lo, red[2 * w], red[2 * w + 1]);
+  }
+}
+
 // Complex pairs of the working precision (the adjoint's accumulators).
 template <typename Real> struct C2;
 template <> struct C2<float> { using T = float2; };
