@@ -833,6 +833,19 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    # the adjoint (qed_eval_grad) of the same plans, on slices of the workload
+    if not args.no_configs:
+        adj = {"sample": "the first 262,144 (mixed) and 65,536 (FP64) points of the workload"}
+        for prec, nn in (("mixed", min(n, 1 << 18)), ("fp64", min(n, 1 << 16))):
+            plan = res[prec]["plan"]
+            mm = d_mom[:nn]
+            oo = torch.empty(nn, dtype=torch.float64, device="cuda")
+            gg = torch.empty((nn, k, 3), dtype=torch.float64, device="cuda")
+            ms_f = time_calls(lambda: plan.eval(mm, oo), 3, 1)
+            ms_g = time_calls(lambda: plan.eval_grad(mm, oo, gg), 3, 1)
+            adj[prec] = {"n_points": nn, "points_per_s": nn / (ms_g * 1e-3), "ms": ms_g,
+                         "forward_ms": ms_f, "adjoint_over_forward_time": ms_g / ms_f}
+        line["adjoint"] = adj
     checks = []
     if not args.no_configs:
         line["configs"], checks = config_legs(peaks, steps=3)
