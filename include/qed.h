@@ -117,11 +117,13 @@ typedef struct {
  *     the same schedule when the library is built (csrc/qed_codegen.cpp),
  *     with every instruction expanded into straight-line code whose
  *     photon, polarisation, source, destination and propagator are
- *     literals.  One fixed state in mixed precision, k <= 6: the
+ *     literals.  One fixed state, k <= 6 (both precisions): the
  *     register-join kernel (csrc/qed_fix.cu) on the schedule that keeps
  *     every level below the leaves; per photon set each lane of one warp
  *     builds one leaf, keeps a left leaf in registers and joins it with
- *     every right leaf of the set, from per-lane items of two ints.
+ *     every right leaf of the set, from per-lane items of two ints.  A new
+ *     plan starts in this form, except one fixed state in FP64 with k >= 5,
+ *     where the table-driven kernel measured faster.
  * Both compute the same DAG; their results agree to rounding. */
 typedef enum { QED_KERNEL_TABLE = 0, QED_KERNEL_SPECIALISED = 1 } qed_kernel_form;
 
@@ -238,7 +240,7 @@ qed_status qed_plan_info(qed_plan_t plan, qed_plan_info_t* info);
 
 /* Selects the forward kernel form (qed_kernel_form) that qed_eval,
  * qed_eval_host and qed_cross_section launch.  A new plan starts with the
- * specialised form where it has one.  The switch is atomic: an evaluation
+ * specialised form where it has one (see qed_kernel_form for the exception).  The switch is atomic: an evaluation
  * running on another stream uses one form or the other.
  * Errors: QED_EINVAL (NULL plan, unknown form), QED_EUNSUPPORTED (the plan
  * has no such form).  The paper has no counterpart: its framework emits

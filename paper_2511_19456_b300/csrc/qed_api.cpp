@@ -373,8 +373,8 @@ cudaError_t configure_form(qed_plan_s::Form* f, int sms) {
   return e;
 }
 
-// One fixed state, FP32-mixed: the register-join form (qed_fix.cu), on the
-// schedule that keeps every level below the leaves.  Items are two ints:
+// One fixed state: the register-join form (qed_fix.cu), on the schedule
+// that keeps every level below the leaves.  Items are two ints:
 //   source current | destination current << 16 (0xffff: kept in registers),
 //   polarisation vector | propagator photon set << 8 | side << 24,
 // with the fixed spinors u and ubar as currents 0 and 1 and the schedule's
@@ -388,8 +388,8 @@ cudaError_t configure_form(qed_plan_s::Form* f, int sms) {
 // a propagator name photon set 0 (the kernel's identity entry).  Leaves the
 // plan without the form where the kernel or the schedule's shape does not
 // allow it.
-qed_status setup_fixed_join(qed_plan_s* P, int dev_smem, int sms) {
-  const KernelChoice kc = fixed_join_kernel(P->k);
+qed_status setup_fixed_join(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
+  const KernelChoice kc = fixed_join_kernel(P->k, mixed);
   if (!kc.fn) return QED_OK;
   const int k = P->k, n = k + 1, h = (n + 1) / 2, r = n - h;
   const int team = kc.team;
@@ -446,7 +446,7 @@ qed_status setup_fixed_join(qed_plan_s* P, int dev_smem, int sms) {
     w.push_back(0xffffu << 16);
     w.push_back(0);
   }
-  const int bytes = team_layout(k, 4, ncur).bytes;
+  const int bytes = team_layout(k, mixed ? 4 : 8, ncur).bytes;
   qed_plan_s::Form f{kc, 128, 0, 0, false, bytes};
   f.smem = (size_t)(f.block / team) * bytes;
   while (f.smem > (size_t)dev_smem && f.block > team) {
@@ -469,8 +469,14 @@ qed_status setup_fixed_join(qed_plan_s* P, int dev_smem, int sms) {
 }
 
 // The form a new plan starts with, from measurements on B300: the
-// straight-line specialised kernel wherever it exists.
-int default_form(const qed_plan_s* P) { return P->forms[1].ok ? 1 : 0; }
+// specialised kernel wherever it exists, except the FP64 register-join
+// kernel of one fixed state for k >= 5 (the table kernel, bound by the FP64
+// pipe, is faster there: k = 6, 2.87 against 2.66 M points/s).
+int default_form(const qed_plan_s* P) {
+  if (!P->forms[1].ok) return 0;
+  if (!P->summed && P->prec == QED_FP64 && P->k >= 5) return 0;
+  return 1;
+}
 
 }  // namespace
 
@@ -670,8 +676,8 @@ qed_status create_plan(const qed_process* process, const qed_spin_cfg* spin, qed
       }
     }
   }
-  if (!rewrite && !P->summed && mixed) {
-    qed_status fs = setup_fixed_join(P, dev_smem, sms);
+  if (!rewrite && !P->summed) {
+    qed_status fs = setup_fixed_join(P, mixed, dev_smem, sms);
     if (fs != QED_OK) { free_plan(P); return fs; }
   }
   P->form.store(default_form(P));

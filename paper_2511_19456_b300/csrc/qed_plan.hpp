@@ -31,9 +31,9 @@ struct SpecKernel {
   int team, ncur, team_bytes;
 };
 SpecKernel spec_forward_kernel(int k, bool mixed);
-// One fixed state, FP32-mixed, register-join form (qed_fix.cu), k = 1..6;
-// fn == nullptr otherwise.
-KernelChoice fixed_join_kernel(int k);
+// One fixed state, register-join form (qed_fix.cu), k = 1..6, FP32-mixed or
+// FP64; fn == nullptr otherwise.
+KernelChoice fixed_join_kernel(int k, bool mixed);
 // Adjoint on the distributively rewritten DAG (qed_radj.cu): spin-summed
 // k <= 5 and one fixed state k <= 7; fn == nullptr otherwise.
 KernelChoice radj_kernel(int k, bool summed, bool mixed);

@@ -1,5 +1,5 @@
-"""One fixed spin state in FP32-mixed precision: the register-join kernel
-(qed_fix.cu; the plan's "specialised" form for k <= 6) through the C-ABI,
+"""One fixed spin state: the register-join kernel (qed_fix.cu; the plan's
+"specialised" form for k <= 6, FP32-mixed and FP64) through the C-ABI,
 against the FP64 oracle on the same seeded inputs at the mixed tolerance of
 test_gpu_parity (with the chain bound of tests/error_model.py for the rare
 point next to a propagator pole, in both forms), and against the
@@ -14,7 +14,7 @@ import pytest
 from paper_2511_19456_b300 import Plan, phasespace as ps
 
 from tests.error_model import check_mixed_fixed
-from tests.test_gpu_parity import MIXED_MEDIAN_Z, check_mixed_median, fixed_hel, mixed_tol, mixed_z, run
+from tests.test_gpu_parity import MIXED_MEDIAN_Z, check_mixed_median, fixed_hel, fp64_tol, mixed_tol, mixed_z, run
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -143,6 +143,41 @@ def test_fixed_join_graph_capture():
     assert torch.equal(out, eager)
 
 
-def test_fixed_fp64_and_k7_have_only_the_table_form():
-    assert Plan(4, summed=False, hel=states(4)[0]).kernel_forms() == ["table"]
+def test_k7_has_only_the_table_form():
     assert Plan(7, summed=False, hel=states(7)[0], precision="mixed").kernel_forms() == ["table"]
+    assert Plan(7, summed=False, hel=states(7)[0]).kernel_forms() == ["table"]
+
+
+@pytest.mark.parametrize("k,omega,npts", CASES)
+def test_fixed_join_fp64_vs_oracle(orc, k, omega, npts):
+    """The FP64 register-join kernel: every point within max(1e-12, 64 u64
+    kappa) of the oracle, for the three fixed states; and within rounding of
+    the table kernel.  A new FP64 plan starts in it for k <= 4 (the table
+    kernel, bound by the FP64 pipe, is faster for k >= 5)."""
+    mom = ps.points(k, npts, omega, seed=4200 + k)
+    d = torch.from_numpy(mom).cuda()
+    for hel in states(k):
+        plan = Plan(k, summed=False, hel=hel)
+        assert plan.kernel_forms() == ["table", "specialised"]
+        assert plan.kernel_form == ("specialised" if k <= 4 else "table")
+        plan.set_kernel_form("specialised")
+        ref, kap = orc.m2(mom, sum_mask=0, hel=hel, kappa=True)
+        got = plan.eval(d).cpu().numpy()
+        plan.set_kernel_form("table")
+        tab = plan.eval(d).cpu().numpy()
+        rel = np.abs(got / ref - 1.0)
+        print(f"\nfixed join fp64 k={k} hel={hel}: n={npts} max {rel.max():.3e} (kappa max {kap.max():.1f})")
+        bad = np.nonzero(rel > fp64_tol(kap))[0]
+        assert bad.size == 0, (bad[:5], rel[bad[:5]], kap[bad[:5]])
+        assert np.all(np.abs(got / tab - 1.0) <= 2 * fp64_tol(kap))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 127, 1000, 4099])
+def test_fixed_join_fp64_ragged_sizes(orc, n):
+    hel = states(6)[1]
+    mom = ps.points(6, n, 8.0, seed=81)
+    plan = Plan(6, summed=False, hel=hel)
+    plan.set_kernel_form("specialised")
+    got = run(plan, mom)
+    ref, kap = orc.m2(mom, sum_mask=0, hel=hel, kappa=True)
+    assert np.all(np.abs(got / ref - 1.0) <= fp64_tol(kap))

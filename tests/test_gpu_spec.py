@@ -117,12 +117,14 @@ def test_tune_picks_a_form_and_stays_correct(orc, k, precision):
 
 
 def test_which_plans_have_the_specialised_form():
-    # one fixed state: only the mixed form has one (the register-join kernel)
-    fixed = Plan(3, summed=False, hel=[1, 2, -1, 1, 2, 1])
-    assert fixed.kernel_forms() == ["table"]
-    assert Plan(3, summed=False, hel=[1, 2, -1, 1, 2, 1], precision="mixed").kernel_forms() == ["table", "specialised"]
+    # one fixed state, k <= 6: the register-join kernel, in both precisions;
+    # k = 7 and the rewritten DAG have only the table form
+    for prec in ("fp64", "mixed"):
+        assert Plan(3, summed=False, hel=[1, 2, -1, 1, 2, 1], precision=prec).kernel_forms() == ["table", "specialised"]
+    fixed7 = Plan(7, summed=False, hel=[1, 1, 1] + [1] * 7)
+    assert fixed7.kernel_forms() == ["table"]
     with pytest.raises(QedError) as ei:
-        fixed.set_kernel_form("specialised")
+        fixed7.set_kernel_form("specialised")
     assert ei.value.status == QED_EUNSUPPORTED
     assert Plan(4, rewrite=True).kernel_forms() == ["table"]
     assert Plan(5).kernel_forms() == ["table"]
