@@ -34,10 +34,10 @@ qed_fwd_kernel(const KParams p) {
                                         smem);
 }
 
-// Spin-summed, k other than 4 and 7: launch bounds that allow up to 128
-// registers per thread (the compiler's own choice under the one-argument
-// bounds spilled a few bytes at k = 1, 3, 5, 6; k = 4 and 7 are tuned with
-// those bounds and keep them).
+// Spin-summed, k other than 4 (and mixed k = 7): launch bounds that allow
+// up to 128 registers per thread (the compiler's own choice under the
+// one-argument bounds spilled a few bytes at k = 1, 3, 5, 6 and, with the
+// packed joins, at mixed k = 7; k = 4 and FP64 k = 7 keep those bounds).
 template <int K, typename Real, int TEAM>
 __global__ void __launch_bounds__(TEAM > 32 ? TEAM : 256, 65536 / ((TEAM > 32 ? TEAM : 256) * 128))
 qed_fwd_summed_kernel(const KParams p) {
@@ -103,7 +103,11 @@ KernelChoice pick(bool mixed) {
   } else {
     if (mixed) {
       constexpr int T = team_of<K, SUMMED, true>();
-      return {qed_fwd_kernel<K, SUMMED, float, T, es_of<K, SUMMED, true>()>, T};
+      // k = 7: the packed joins spill under the one-argument bounds (the
+      // compiler settles on 80 registers); two 256-thread blocks per SM are
+      // all shared memory holds anyway, so allow 128
+      if constexpr (K == 7) return {qed_fwd_summed_kernel<K, float, T>, T};
+      else return {qed_fwd_kernel<K, SUMMED, float, T, es_of<K, SUMMED, true>()>, T};
     }
     constexpr int T = team_of<K, SUMMED, false>();
     return {qed_fwd_kernel<K, SUMMED, double, T, es_of<K, SUMMED, false>()>, T};
