@@ -43,7 +43,7 @@ PEAK_FP64_TFLOPS = 1.25
 # FWD: the table-driven kernel (qed_fwd.cu); SPEC: the straight-line
 # specialised kernel (the kernel version its generator writes).
 FWD_KERNEL_VERSION = "fwd-6"
-SPEC_KERNEL_VERSION = "spec-3"
+SPEC_KERNEL_VERSION = "spec-4"
 # Mixed-precision and FP64 per-point bounds against the oracle (as the GPU
 # tests state them): 64 u32 max(kappa, 1) and max(1e-12, 64 u64 kappa).
 U32, U64 = 2.0 ** -24, 2.0 ** -53

@@ -113,7 +113,7 @@ typedef struct {
  *     plan's linear schedule (instruction, phase and photon-set tables) from
  *     device memory at run time.  Every plan has it.
  *   QED_KERNEL_SPECIALISED: a kernel shaped for the plan's kind.
- *     Spin-summed plans of the node-reduced DAG with k <= 4: generated from
+ *     Spin-summed plans of the node-reduced DAG with k <= 5: generated from
  *     the same schedule when the library is built (csrc/qed_codegen.cpp),
  *     with every instruction expanded into straight-line code whose
  *     photon, polarisation, source, destination and propagator are
@@ -331,8 +331,7 @@ void qed_plan_destroy(qed_plan_t plan);
  * reset and the launch are captured once in a CUDA graph.  Kernel forms as
  * for a plan (qed_kernel_form): QED_KERNEL_TABLE runs the table-driven point
  * evaluation of every k, QED_KERNEL_SPECIALISED (a new batch's form) the
- * straight-line specialised one for k <= 4 and the table-driven one for
- * k = 5.  The batch keeps the plans (they must outlive it), allocates its
+ * straight-line specialised one of every k.  The batch keeps the plans (they must outlive it), allocates its
  * item list, request table and counter, and is not safe for concurrent use
  * from two streams.
  * Errors: QED_EINVAL (NULL, n < 0, mixed precisions), QED_EUNSUPPORTED

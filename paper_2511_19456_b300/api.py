@@ -376,7 +376,7 @@ class Batch:
         return {"block": b.value, "work_target_flops": t.value, "n_items": n.value, "kernel_form": form}
 
     def set_kernel_form(self, form: str) -> None:
-        """"table" or "specialised" (straight-line points for k <= 4)."""
+        """"table" or "specialised" (straight-line points for every k)."""
         check(_lib.lib().qed_batch_set_kernel_form(self._h, Plan.KERNEL_FORMS[form]), "qed_batch_set_kernel_form")
 
     def close(self):

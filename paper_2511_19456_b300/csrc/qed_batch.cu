@@ -10,8 +10,7 @@
 // CUDA graph and replayed; per call only the request table (device pointers
 // of momenta and outputs) is copied.  Two kernel forms, as for a plan: the
 // table-driven point evaluation for every k, or the straight-line
-// specialised one for k <= 4 (generated at build time; k = 5 stays
-// table-driven).  qed_batch_tune times every form, block size and item size
+// specialised one (generated at build time).  qed_batch_tune times every form, block size and item size
 // of a small grid on the caller's buffers and keeps the fastest.
 #include <cuda_runtime.h>
 
@@ -72,9 +71,9 @@ BatchFn batch_fn(bool mixed, int form) {
 }
 
 // Shared memory per team of a request's points in a form: the specialised
-// kernel's own layout for k <= 4, else the plan's table kernel layout.
+// kernel's own layout where it has one, else the plan's table kernel layout.
 int team_bytes_of(const qed_plan_s* P, int form) {
-  if (form == QED_KERNEL_SPECIALISED && P->k <= 4) {
+  if (form == QED_KERNEL_SPECIALISED) {
     const SpecKernel sk = spec_forward_kernel(P->k, P->prec == QED_MIXED);
     if (sk.fn) return sk.team_bytes;
   }

@@ -54,7 +54,7 @@ using BatchFn = void (*)(const BatchDesc*, const BatchItem*, int, unsigned*);
 
 // The specialised form of the batched kernel (generated with the
 // straight-line forward kernels): the same work-item loop, with the
-// straight-line point evaluation for k <= 4.
+// straight-line point evaluation of every k.
 BatchFn batch_spec_kernel(bool mixed);
 
 // The largest dynamic shared memory a launch of fn may ask for: the device's

@@ -3,7 +3,7 @@
 // The paper's framework compiles the scheduled CDAG into one function of
 // straight-line code, every task inlined (Sec. II-A, the code generation
 // step; Sec. III-D measures full inlining against calls).  This program does
-// the same for the spin-summed plans of k = 1..4: it builds the node-reduced
+// the same for the spin-summed plans of k = 1..5: it builds the node-reduced
 // DAG and its linear schedule (dag.cpp: generate, reduce, build_schedule) and
 // writes one CUDA kernel per k and precision in which every instruction of the
 // schedule is expanded into the items of one round of the team's lanes, with
@@ -31,7 +31,7 @@ namespace {
 
 // Version of the generated kernels (layout, rounds, joins); part of the
 // benchmark's record of which kernel a counter capture belongs to.
-constexpr const char* SPEC_VERSION = "spec-3";
+constexpr const char* SPEC_VERSION = "spec-4";
 
 // One vertex (+ propagation) node of a range.  photon, src and post are C++
 // expressions: literals for the kept currents, entries of the photon set's
@@ -226,10 +226,10 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
   kd.team = team;
   kd.ncur = ncur;
   kd.team_bytes = L.bytes;
-  kd.block = team > 32 ? team : 128;
+  kd.block = team > 128 ? team : 128;
   // resident blocks to compile for: as many as shared memory allows, but
-  // never fewer than 96 registers per thread in FP32 (the k = 4 joins hold
-  // the right leaves, a left leaf and 16 accumulators in registers) or 160 in
+  // never fewer than 96 registers per thread in FP32 (the joins hold a block
+  // of right leaves, a left leaf and 16 accumulators in registers) or 160 in
   // FP64
   const int min_regs = mixed ? 96 : 160;
   kd.min_blocks = std::max(1, std::min(65536 / (kd.block * min_regs), blocks_by_smem((kd.block / team) * L.bytes)));
@@ -350,11 +350,13 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
   o << "  " << R << "* s_spin = reinterpret_cast<" << R << "*>(base + L.spin);\n";
   o << "  double* s_red = reinterpret_cast<double*>(base + L.red);\n";
   o << "  " << R << "* s_cur = reinterpret_cast<" << R << "*>(base + L.cur);\n";
-  if (mixed)
+  // the FP64-light mixed set-up takes at most two photons per denominator
+  // (n <= 5); otherwise, and in FP64, the table kernels' set-up
+  if (mixed && n / 2 <= 2)
     o << "  spec::setup_f32<K, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
       << "      reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));\n";
   else
-    o << "  point_setup<K, double, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
+    o << "  point_setup<K, " << R << ", TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,\n"
       << "      reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));\n";
   o << "  Acc<" << R << "> acc[4];\n";
   for (int ph = 0; ph < sc.n_stored_phases; ++ph) {
@@ -408,18 +410,27 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
     return v;
   };
   auto emit_rounds = [&](const std::vector<std::string>& rs) { for (const std::string& x : rs) o << x; };
+  // right leaves per block of the FP32 joins: all of them up to two (k <= 4),
+  // else two at a time (k = 5: six right leaves; 64 registers a block)
+  const int BB = NR <= 2 ? NR : 2;
+  if (NR % BB != 0) throw std::runtime_error("right leaves not in whole blocks");
+  // rbase < 0: the right leaves of an even set at leaf_r, of an odd one at
+  // dead_base (sets in pairs)
   auto join = [&](const std::string& set_index, int rbase) {
     o << "    {\n";
     o << "      const unsigned tv = __ldg(p.lane_tab + ((" << set_index << ") << " << n
       << ") + lane);   // pext(lane, S) | pext(lane, ~S) << 8\n";
     o << "      const int pl = (int)(tv & 0xffu), pr = (int)(tv >> 8);\n";
+    const std::string rb = rbase >= 0 ? std::to_string(rbase * 8)
+                                      : "((" + set_index + ") & 1 ? " + std::to_string(dead_base * 8) + " : " +
+                                            std::to_string(leaf_r * 8) + ")";
     if (mixed)
-      o << "      spec::join_set_f32<" << NL << ", " << NR << ", " << NPL << ", " << NPR
+      o << "      spec::join_set_f32<" << NL << ", " << NR << ", " << NPL << ", " << NPR << ", " << BB
         << ">(reinterpret_cast<const float4*>(s_cur + " << leaf_l * 8 << ") + pl,\n"
-        << "          reinterpret_cast<const float4*>(s_cur + " << rbase * 8 << ") + pr, acc);\n";
+        << "          reinterpret_cast<const float4*>(s_cur + " << rb << ") + pr, acc);\n";
     else
       o << "      spec::join_set_f64<" << NL << ", " << NR << ", " << NPL << ", " << NPR << ">(s_cur + " << leaf_l * 8
-        << " + pl * 4, s_cur + " << rbase * 8 << " + pr * 4, acc);\n";
+        << " + pl * 4, s_cur + " << rb << " + pr * 4, acc);\n";
     o << "    }\n";
     o << "    team_sync<TEAM>();\n";
   };
@@ -431,24 +442,63 @@ KernelDesc emit_kernel(std::ostringstream& out, int k, bool mixed) {
   if (!paired) {
     o << "  for (int s = 0; s < " << nsets << "; ++s) {\n";
     o << "    const " << TT << "& cs = " << tab << "[s];\n";
-    emit_rounds(em.rounds(left_body("cs"), 0, h, false, true, leaf_l, NPL, "left leaves"));
-    emit_rounds(em.rounds(right_body("cs", leaf_r), 1, r, true, true, leaf_r, NPR,
-                          "right leaves (S2 propagation hoisted)"));
+    std::vector<Item> lv = left_body("cs"), rv = right_body("cs", leaf_r);
+    // a team of two warps (k = 5): where each side's last round fills at
+    // most one warp, the first warp takes the left tail and the second the
+    // right tail in one round (warp-uniform branches) instead of two half
+    // rounds
+    const int nvl = 1 << (h + 1);
+    const int tl = nvl < team ? NL % (team / nvl) : 0, tr = nvr < team ? NR % (team / nvr) : 0;
+    const bool split = team == 64 && tl > 0 && tr > 0 && tl * nvl <= 32 && tr * nvr <= 32;
+    std::vector<Item> ltail, rtail;
+    if (split) {
+      for (int i = NL - tl; i < NL; ++i) {
+        ltail.push_back(lv[i]);
+        ltail.back().leaf_base = leaf_l;
+        ltail.back().leaf_pos = i;
+      }
+      for (int i = NR - tr; i < NR; ++i) rtail.push_back(rv[i]);   // leaf_base, leaf_pos set
+      lv.resize(NL - tl);
+      rv.resize(NR - tr);
+    }
+    emit_rounds(em.rounds(lv, 0, h, false, true, leaf_l, NPL, "left leaves"));
+    emit_rounds(em.rounds(rv, 1, r, true, true, leaf_r, NPR, "right leaves (S2 propagation hoisted)"));
+    if (split) {
+      o << "    if (lane < 32) {\n";
+      em.team = 32;
+      em.indent = "      ";
+      emit_rounds(em.rounds(ltail, 0, h, false, true, leaf_l, NPL, "left leaves, first warp"));
+      o << "    } else {\n";
+      o << "      const int lane_w1 = lane - 32;\n";
+      o << "      {\n";
+      o << "        const int lane = lane_w1;\n";
+      em.indent = "        ";
+      emit_rounds(em.rounds(rtail, 1, r, true, true, leaf_r, NPR,
+                            "right leaves, second warp (S2 propagation hoisted)"));
+      o << "      }\n";
+      o << "    }\n";
+      em.team = team;
+      em.indent = "    ";
+    }
     o << "    team_sync<TEAM>();\n";
     join("s", leaf_r);
   } else {
-    o << "  for (int s = 0; s < " << nsets << "; s += 2) {\n";
-    o << "    const " << TT << "& ca = " << tab << "[s];\n";
-    o << "    const " << TT << "& cb = " << tab << "[s + 1];\n";
-    std::vector<Item> rr = right_body("ca", leaf_r);
+    // one set per iteration, one copy of the left rounds and of the join: an
+    // even set also builds the right leaves of the odd set after it, whose
+    // join then reads them from the first kept level
+    o << "  for (int s = 0; s < " << nsets << "; ++s) {\n";
+    o << "    const " << TT << "& cs = " << tab << "[s];\n";
+    o << "    if ((s & 1) == 0) {\n";
+    o << "      const " << TT << "& cb = " << tab << "[s + 1];\n";
+    std::vector<Item> rr = right_body("cs", leaf_r);
     for (const Item& it : right_body("cb", dead_base)) rr.push_back(it);
-    emit_rounds(em.rounds(rr, 1, r, true, true, leaf_r, NPR, "right leaves of both sets (S2 propagation hoisted)"));
-    emit_rounds(em.rounds(left_body("ca"), 0, h, false, true, leaf_l, NPL, "left leaves, first set"));
+    em.indent = "      ";
+    emit_rounds(em.rounds(rr, 1, r, true, true, leaf_r, NPR, "right leaves of this set and the next (S2 propagation hoisted)"));
+    em.indent = "    ";
+    o << "    }\n";
+    emit_rounds(em.rounds(left_body("cs"), 0, h, false, true, leaf_l, NPL, "left leaves"));
     o << "    team_sync<TEAM>();\n";
-    join("s", leaf_r);
-    emit_rounds(em.rounds(left_body("cb"), 0, h, false, true, leaf_l, NPL, "left leaves, second set"));
-    o << "    team_sync<TEAM>();\n";
-    join("s + 1", dead_base);
+    join("s", -1);
   }
   em.indent = "  ";
   o << "  }\n";
@@ -482,7 +532,7 @@ int main(int argc, char** argv) {
   out << "// GENERATED by qed_codegen.cpp from the node-reduced DAG and its linear\n"
       << "// schedule (dag.cpp); do not edit.  Kernel version " << SPEC_VERSION << ".\n"
       << "//\n"
-      << "// Straight-line specialised forward kernels, spin-summed, k = 1..4: every\n"
+      << "// Straight-line specialised forward kernels, spin-summed, k = 1..5: every\n"
       << "// vertex (+ propagation) instruction of the schedule expanded into rounds of\n"
       << "// the team's lanes with literal photon, polarisation rank, source,\n"
       << "// destination and propagator; the S2 joins of each photon set on the leaf\n"
@@ -490,21 +540,19 @@ int main(int argc, char** argv) {
       << "#include \"qed_spec.cuh\"\n#include \"qed_plan.hpp\"\n#include \"qed_batch.cuh\"\n\nnamespace qed {\n\n";
   std::vector<KernelDesc> kds;
   try {
-    for (int k = 1; k <= 4; ++k)
+    for (int k = 1; k <= 5; ++k)
       for (int mixed = 1; mixed >= 0; --mixed) kds.push_back(emit_kernel(out, k, mixed != 0));
   } catch (const std::exception& e) {
     std::fprintf(stderr, "qed_codegen: %s\n", e.what());
     return 1;
   }
   // the batched evaluation's specialised form: the persistent work-item loop
-  // of qed_batch_kernel (qed_batch.cuh) with the straight-line points for
-  // k <= 4 and the table-driven ones for k = 5; each item kind is a call of
-  // its own (not inlined), so that registers are allocated per kind rather
-  // than for their union
+  // of qed_batch_kernel (qed_batch.cuh) with the straight-line points; each
+  // item kind is a call of its own (not inlined), so that registers are
+  // allocated per kind rather than for their union
   out << "// The batched evaluation (requests of k = 1..5 in one persistent launch),\n"
       << "// specialised form: the work-item loop of qed_batch_kernel with the\n"
-      << "// straight-line point evaluation above for k <= 4; k = 5 has no\n"
-      << "// specialised kernel and runs the table-driven one.  One item's points\n"
+      << "// straight-line point evaluation above for every k.  One item's points\n"
       << "// per call, each kind of item a function of its own (called, not\n"
       << "// inlined: registers are allocated per kind, not for their union).\n"
       << "template <int K, typename Real>\n"
@@ -512,7 +560,7 @@ int main(int argc, char** argv) {
       << "                                             unsigned char* smem) {\n"
       << "  constexpr int TEAM = 1 << (K + 1);\n"
       << "  const int lane = threadIdx.x & (TEAM - 1), team = threadIdx.x / TEAM, tpc = blockDim.x / TEAM;\n";
-  for (int k = 1; k <= 4; ++k) {
+  for (int k = 1; k <= 5; ++k) {
     int tb32 = 0, tb64 = 0;
     for (const KernelDesc& kd : kds)
       if (kd.k == k) (kd.mixed ? tb32 : tb64) = kd.team_bytes;
@@ -528,10 +576,7 @@ int main(int argc, char** argv) {
         << "    }\n"
         << "  }\n";
   }
-  out << "  else {\n"
-      << "    eval_range<K, true, Real, TEAM, 1>(kp, p0, p1, (long long)(blockDim.x / TEAM), smem);\n"
-      << "  }\n"
-      << "}\n\n"
+  out << "}\n\n"
       << "template <typename Real>\n"
       << "__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1)\n"
       << "qed_batch_spec_kernel(const BatchDesc* __restrict__ reqs, const BatchItem* __restrict__ items,\n"

@@ -24,7 +24,7 @@ KernelChoice tape_kernel();
 cudaError_t launch_forward(void (*fn)(const KParams), int grid, int block, size_t smem,
                            cudaStream_t st, const KParams& p);
 // Straight-line specialised forward kernel (generated at build time by
-// qed_codegen.cpp): spin-summed, k = 1..4; fn == nullptr where none exists.
+// qed_codegen.cpp): spin-summed, k = 1..5; fn == nullptr where none exists.
 // ncur and team_bytes: the currents and shared memory per team it expects.
 struct SpecKernel {
   void (*fn)(const KParams);

@@ -263,63 +263,74 @@ __device__ __forceinline__ void vs_item(const Real* xs, const Real* e, const Rea
 //
 // Packed FP32 FMAs (two lanes of arithmetic per instruction): with
 // L_c = (lr, li) and R_c = (rr, ri), the right leaves held in registers as
-// (rr, rr) and (ri, ri) for the whole set,
+// (rr, rr) and (ri, ri),
 //   A += (rr, rr) * (lr, li),  B += (ri, ri) * (lr, li)
 // so that A = (sum rr lr, sum rr li), B = (sum ri lr, sum ri li) and
 //   Re M = A.x - B.y,  Im M = A.y + B.x.
-// A starts from minus the accumulator's compensation (the first step of the
-// Kahan update), B from zero.
-template <int NL, int NR, int NPL, int NPR>
+// The right leaves are taken BB at a time (all NR where they fit in
+// registers); each block is one compensated step per state over its
+// NL x BB diagrams: A starts from minus the accumulator's compensation (the
+// first step of the Kahan update), B from zero.
+template <int NL, int NR, int NPL, int NPR, int BB = NR>
 __device__ __forceinline__ void join_set_f32(const float4* L, const float4* R, Acc<float> acc[4]) {
-  float2 rr[NR][2][4], ri[NR][2][4];
+  static_assert(NR % BB == 0, "whole blocks of right leaves");
+  // blocks one after another (not unrolled: the registers of one block)
+#pragma unroll 1
+  for (int b0 = 0; b0 < NR; b0 += BB) {
+    float2 rr[BB][2][4], ri[BB][2][4];
 #pragma unroll
-  for (int b = 0; b < NR; ++b)
+    for (int bb = 0; bb < BB; ++bb)
 #pragma unroll
-    for (int so = 0; so < 2; ++so) {
-      const float4 c0 = R[((b * 2 + 0) * 2 + so) * NPR], c1 = R[((b * 2 + 1) * 2 + so) * NPR];
-      const float re[4] = {c0.x, c0.z, c1.x, c1.z}, im[4] = {c0.y, c0.w, c1.y, c1.w};
+      for (int so = 0; so < 2; ++so) {
+        const int b = b0 + bb;
+        const float4 c0 = R[((b * 2 + 0) * 2 + so) * NPR], c1 = R[((b * 2 + 1) * 2 + so) * NPR];
+        const float re[4] = {c0.x, c0.z, c1.x, c1.z}, im[4] = {c0.y, c0.w, c1.y, c1.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        rr[b][so][c] = make_float2(re[c], re[c]);
-        ri[b][so][c] = make_float2(im[c], im[c]);
+        for (int c = 0; c < 4; ++c) {
+          rr[bb][so][c] = make_float2(re[c], re[c]);
+          ri[bb][so][c] = make_float2(im[c], im[c]);
+        }
       }
+    float2 A[2][2], B[2][2];
+#pragma unroll
+    for (int si = 0; si < 2; ++si)
+#pragma unroll
+      for (int so = 0; so < 2; ++so) {
+        A[si][so] = make_float2(-acc[si * 2 + so].cre, -acc[si * 2 + so].cim);
+        B[si][so] = make_float2(0.f, 0.f);
+      }
+    // all left leaves at once where the right leaves fit whole, else two
+    // (the registers of the loads in flight)
+    constexpr int UA = BB == NR ? NL : 2;
+#pragma unroll (UA)
+    for (int a = 0; a < NL; ++a) {
+      float2 l[2][4];
+#pragma unroll
+      for (int si = 0; si < 2; ++si) {
+        const float4 c0 = L[((a * 2 + 0) * 2 + si) * NPL], c1 = L[((a * 2 + 1) * 2 + si) * NPL];
+        l[si][0] = make_float2(c0.x, c0.y);
+        l[si][1] = make_float2(c0.z, c0.w);
+        l[si][2] = make_float2(c1.x, c1.y);
+        l[si][3] = make_float2(c1.z, c1.w);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int si = 0; si < 2; ++si)
+#pragma unroll
+          for (int bb = 0; bb < BB; ++bb)
+#pragma unroll
+            for (int so = 0; so < 2; ++so) {
+              A[si][so] = __ffma2_rn(rr[bb][so][c], l[si][c], A[si][so]);
+              B[si][so] = __ffma2_rn(ri[bb][so][c], l[si][c], B[si][so]);
+            }
     }
-  float2 A[2][2], B[2][2];
 #pragma unroll
-  for (int si = 0; si < 2; ++si)
+    for (int si = 0; si < 2; ++si)
 #pragma unroll
-    for (int so = 0; so < 2; ++so) {
-      A[si][so] = make_float2(-acc[si * 2 + so].cre, -acc[si * 2 + so].cim);
-      B[si][so] = make_float2(0.f, 0.f);
-    }
-#pragma unroll
-  for (int a = 0; a < NL; ++a) {
-    float2 l[2][4];
-#pragma unroll
-    for (int si = 0; si < 2; ++si) {
-      const float4 c0 = L[((a * 2 + 0) * 2 + si) * NPL], c1 = L[((a * 2 + 1) * 2 + si) * NPL];
-      l[si][0] = make_float2(c0.x, c0.y);
-      l[si][1] = make_float2(c0.z, c0.w);
-      l[si][2] = make_float2(c1.x, c1.y);
-      l[si][3] = make_float2(c1.z, c1.w);
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int si = 0; si < 2; ++si)
-#pragma unroll
-        for (int b = 0; b < NR; ++b)
-#pragma unroll
-          for (int so = 0; so < 2; ++so) {
-            A[si][so] = __ffma2_rn(rr[b][so][c], l[si][c], A[si][so]);
-            B[si][so] = __ffma2_rn(ri[b][so][c], l[si][c], B[si][so]);
-          }
+      for (int so = 0; so < 2; ++so)
+        acc[si * 2 + so].commit(__fsub_rn(A[si][so].x, B[si][so].y), __fadd_rn(A[si][so].y, B[si][so].x));
   }
-#pragma unroll
-  for (int si = 0; si < 2; ++si)
-#pragma unroll
-    for (int so = 0; so < 2; ++so)
-      acc[si * 2 + so].commit(__fsub_rn(A[si][so].x, B[si][so].y), __fadd_rn(A[si][so].y, B[si][so].x));
 }
 
 // The same in FP64 (scalar FMAs, plain accumulation), chunks of 4 doubles.

@@ -1,5 +1,5 @@
 """The build-time code generator of the specialised kernels (no GPU): it runs,
-emits one kernel per k = 1..4 and precision, and its rounds follow the
+emits one kernel per k = 1..5 and precision, and its rounds follow the
 plan's linear schedule: one vertex item per lane group of every
 instruction range, and one join per photon set."""
 import math
@@ -40,32 +40,48 @@ def expected_rounds(k):
     side = {s: int(sc["instr"][ph["beg"][s]]["side"]) for s in range(2) if ph["cnt"][s]}
     left = [s for s in side if side[s] == 0]
     right = [s for s in side if side[s] == 1]
-    lr = rounds_of(ph["cnt"][left[0]], ph["level"][left[0]], team)
+    nl, llev = ph["cnt"][left[0]], ph["level"][left[0]]
     nr, rlev = ph["cnt"][right[0]], ph["level"][right[0]]
+    lr = rounds_of(nl, llev, team)
     # sets in pairs where one set's right leaves fill at most half a round and
-    # the first left level is free once the second is kept (ls >= 2)
+    # the first left level is free once the second is kept (ls >= 2): an even
+    # set's body also builds the next set's right leaves
     paired = 2 * nr * (1 << (rlev + 1)) <= team and n_sets % 2 == 0 and sc["ls"] >= 2
+    # a team of two warps whose left and right tails fit one warp each: the
+    # two tails share one round (one warp each)
+    nvl, nvr = 1 << (llev + 1), 1 << (rlev + 1)
+    tl = nl % (team // nvl) if nvl < team else 0
+    tr = nr % (team // nvr) if nvr < team else 0
+    split = team == 64 and tl > 0 and tr > 0 and tl * nvl <= 32 and tr * nvr <= 32
     if paired:
-        per_body = 2 * lr + rounds_of(2 * nr, rlev, team)
+        per_body = lr + rounds_of(2 * nr, rlev, team)
+    elif split:
+        per_body = (rounds_of(nl - tl, llev, team) + rounds_of(nr - tr, rlev, team)
+                    + rounds_of(tl, llev, 32) + rounds_of(tr, rlev, 32))
     else:
         per_body = lr + rounds_of(nr, rlev, team)
-    return stored, per_body, sc, paired
+    return stored, per_body, sc, paired, split
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("real", ["f32", "f64"])
 def test_rounds_follow_the_schedule(generated, k, real):
     body = kernel_body(generated, k, real)
-    stored, per_body, sc, paired = expected_rounds(k)
+    stored, per_body, sc, paired, split = expected_rounds(k)
     assert body.count("spec::vs_item<") == stored + per_body
-    assert body.count("spec::join_set_") == (2 if paired else 1)
-    assert f"for (int s = 0; s < {len(sc['sets'])}; {'s += 2' if paired else '++s'})" in body
+    assert body.count("spec::join_set_") == 1
+    assert f"for (int s = 0; s < {len(sc['sets'])}; ++s)" in body
     assert paired == (k == 4)
+    assert split == (k == 5)
+    if paired:
+        assert "if ((s & 1) == 0)" in body
+    if split:
+        assert "if (lane < 32)" in body
     # nothing is read from instruction tables at run time
     assert "p.instr" not in body and "ld_instr" not in body
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_set_table_matches_the_schedule(generated, k):
     """Each row of the generated constant table names the set, its
     complement and, per leaf position, the vertex photon of one of the

@@ -38,8 +38,8 @@ def test_batch_matches_standalone_and_oracle(orc, precision, form):
         if n == 0:
             continue
         # the batch runs the point code of the standalone plan in the same
-        # form (k = 5 has only the table form): bit for bit
-        plans[k].set_kernel_form(form if k <= 4 else "table")
+        # form: bit for bit
+        plans[k].set_kernel_form(form)
         ref = plans[k].eval(m)
         torch.cuda.synchronize()
         assert torch.equal(o, ref), (k, n)
