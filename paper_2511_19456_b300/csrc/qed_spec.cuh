@@ -97,9 +97,9 @@ __device__ __forceinline__ void ld3(const double* e, double ev[3]) {
 // whose per-photon adds also issue for lanes without the photon).
 //   1. each lane loads one FP64 momentum component and splits it into a
 //      float-float pair (hi + lo, exact to about 2^-48);
-//   2. the Lorentz invariants, one Minkowski product per lane in FP64:
-//      p.p, p'.p', k_j.k_j, p.k_j, p'.k_j and k_i.k_j (i < j), with the
-//      photon slots k_0 = incoming, k_j (j >= 1) outgoing;
+//   2. the Lorentz invariants (setup_invariants): the Minkowski products
+//      p.p, p'.p', k_j.k_j, p.k_j, p'.k_j and k_i.k_j (i < j), one per lane,
+//      then their signed combinations, one FMA per lane, all in FP64;
 //   3. for the subset T of each lane, the FP64 denominator as the same sum
 //      as Q_T^2 - m^2 in invariants.  With |T| <= n/2 the line is taken
 //      from the incoming electron, Q_T = p + sum_{j in T} sigma_j k_j
@@ -108,19 +108,13 @@ __device__ __forceinline__ void ld3(const double* e, double ev[3]) {
 //      by momentum conservation.  With U the photons summed (at most two)
 //      and tau = sigma (incoming side) or -sigma (outgoing side),
 //        D_T = (q.q - m^2) + sum_{j in U} (k_j.k_j + 2 tau_j q.k_j)
-//              + sum_{i<j in U} 2 tau_i tau_j k_i.k_j,   q = p or p';
-//      the numerator Q_T in float-float (TwoSum on the FP32 pipe), rounded
-//      once; the entries (Q0 +- m)/D and Q/D in FP32;
+//              + sum_{i<j in U} 2 tau_i tau_j k_i.k_j,   q = p or p',
+//      three FP64 additions of combinations; the numerator Q_T in
+//      float-float (TwoSum on the FP32 pipe), rounded once; the entries
+//      (Q0 +- m)/D and Q/D in FP32;
 //   4. u(p, +-), ubar(p', +-) and eps_j (pol 1, 2) in FP32 from the
 //      float-float momenta (E +- m as float-float sums rounded once).
 // Missing photons of U read a zero slot, so every lane runs the same code.
-template <int N>
-__device__ __forceinline__ int photon_slot(int j) { return j == 0 ? 1 : j + 2; }
-
-template <int N>
-__device__ __forceinline__ int pair_index(int i, int j) {   // i < j: k_i.k_j in the product table
-  return 2 + 3 * N + (i * (2 * N - i - 1)) / 2 + (j - i - 1);
-}
 
 template <int K, int TEAM>
 __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long pt, double* s_mom, float* s_q,
@@ -128,6 +122,7 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
   constexpr int N = K + 1, NS = K + 3, NC = NS * 4;
   constexpr unsigned ALL = (1u << N) - 1;
   constexpr int NPROD = 2 + 3 * N + N * (N - 1) / 2;
+  constexpr int ZERO = 2 + 2 * N + N * N;   // the zero slot of the combinations
   static_assert((1 << N) == TEAM, "one lane per photon subset");
   static_assert(N / 2 <= 2, "at most two photons per denominator");
   // 1. momenta (FP64) and their float-float split
@@ -138,27 +133,10 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
     s_momf[i] = hi;
     s_momf[NC + i] = (float)(v - (double)hi);
   }
-  if (lane == 0) s_w[NPROD] = 0.0;
   team_sync<TEAM>();
-  // 2. the invariants
-  for (int it = lane; it < NPROD; it += TEAM) {
-    int a, b;
-    if (it < 2) {
-      a = b = it == 0 ? 0 : 2;
-    } else if (it < 2 + N) {
-      a = b = photon_slot<N>(it - 2);
-    } else if (it < 2 + 3 * N) {
-      a = it < 2 + 2 * N ? 0 : 2;
-      b = photon_slot<N>((it - 2) % N);
-    } else {
-      int r = it - 2 - 3 * N, i = 0;
-      while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
-      a = photon_slot<N>(i);
-      b = photon_slot<N>(i + 1 + r);
-    }
-    s_w[it] = mdot(s_mom + 4 * a, s_mom + 4 * b);
-  }
-  team_sync<TEAM>();
+  // 2. the invariants and their combinations c
+  setup_invariants<N, TEAM>(lane, p.mass, s_mom, s_w);
+  const double* cmb = s_w + NPROD;
   // 3. the subset of this lane
   {
     const unsigned T = (unsigned)lane;
@@ -168,21 +146,17 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
     const int ja = U ? __ffs(U) - 1 : -1;
     const unsigned U2 = U & (U - 1);
     const int jb = U2 ? __ffs(U2) - 1 : -1;
-    // tau_j: sigma_j on the incoming side, -sigma_j on the outgoing side
-    const double sa = ja < 0 ? 0.0 : ((ja == 0) != out ? 1.0 : -1.0);
-    const double sb = jb < 0 ? 0.0 : ((jb == 0) != out ? 1.0 : -1.0);
-    const int qk0 = out ? 2 + 2 * N : 2 + N;
-    const double m = p.mass;
-    double D = fma(-m, m, s_w[out ? 1 : 0]);
-    D += s_w[ja < 0 ? NPROD : 2 + ja];
-    D = fma(2.0 * sa, s_w[ja < 0 ? NPROD : qk0 + ja], D);
-    D += s_w[jb < 0 ? NPROD : 2 + jb];
-    D = fma(2.0 * sb, s_w[jb < 0 ? NPROD : qk0 + jb], D);
-    D = fma(2.0 * sa * sb, s_w[jb < 0 ? NPROD : pair_index<N>(ja, jb)], D);
-    // the numerator in float-float: q + tau_a k_a + tau_b k_b
+    const int so = out ? 2 + N : 2;
+    double D = cmb[out ? 1 : 0];
+    D += cmb[ja < 0 ? ZERO : so + ja];
+    D += cmb[jb < 0 ? ZERO : so + jb];
+    D += cmb[jb < 0 ? ZERO : 2 + 2 * N + ja * N + jb];
+    // the numerator in float-float: q + tau_a k_a + tau_b k_b, with tau_j =
+    // sigma_j on the incoming side and -sigma_j on the outgoing side
     const int qs = out ? 2 : 0;
-    const int ka = photon_slot<N>(ja < 0 ? 0 : ja), kb = photon_slot<N>(jb < 0 ? 0 : jb);
-    const float ta = (float)sa, tb = (float)sb;
+    const int ka = photon_slot_of(ja < 0 ? 0 : ja), kb = photon_slot_of(jb < 0 ? 0 : jb);
+    const float ta = ja < 0 ? 0.f : ((ja == 0) != out ? 1.f : -1.f);
+    const float tb = jb < 0 ? 0.f : ((jb == 0) != out ? 1.f : -1.f);
     float qh[4], ql[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -198,7 +172,7 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
     }
     const bool used = T != 0 && T != ALL;
     const float inv = used ? 1.0f / (float)D : 0.0f;
-    const float mf = (float)m;
+    const float mf = (float)p.mass;
     // Q0 -+ m: the high part first (exact where Q0 is close to m)
     d[0] = __fadd_rn(__fadd_rn(qh[0], mf), ql[0]) * inv;
     d[1] = __fadd_rn(__fsub_rn(qh[0], mf), ql[0]) * inv;
@@ -219,7 +193,7 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
       store8(s_spin + (side * 2 + e) * 8, sp);
     } else {
       const int j = (it - 4) >> 1, pb = (it - 4) & 1;
-      const float* h = s_momf + 4 * photon_slot<N>(j);
+      const float* h = s_momf + 4 * photon_slot_of(j);
       float ev[3];
       make_pol_core<float>(h[1], h[2], h[3], pb, ev);
       float* d = s_eps + (j * 2 + pb) * 4;

@@ -230,14 +230,86 @@ __device__ __forceinline__ double mdot(const double* a, const double* b) {
   return fma(a[0], b[0], fma(-a[1], b[1], fma(-a[2], b[2], -a[3] * b[3])));
 }
 
+// Momentum slot of photon j (slot 1: the incoming photon, j = 0).
+__device__ __forceinline__ int photon_slot_of(int j) { return j == 0 ? 1 : j + 2; }
+
+// The Lorentz invariants of one point from which the mixed form sums every
+// propagator denominator, in FP64 (a3).  Photon j sits in momentum slot 1
+// (j = 0, incoming) or j + 2; sigma_0 = +1, sigma_j = -1 (j >= 1).
+//   1. the Minkowski products, one per lane and item, so that every lane
+//      issues the same four FP64 instructions:
+//        w[0] = p.p, w[1] = p'.p', w[2 + j] = k_j.k_j, w[2 + N + j] = p.k_j,
+//        w[2 + 2N + j] = p'.k_j, w[2 + 3N + r] = k_a.k_b (a < b, r the
+//        rank of (a, b) in row order);
+//   2. their signed combinations, one FMA per lane and item, at
+//      c = w + n_products(N):
+//        c[0], c[1] = q.q - m^2 (q = p, p'),
+//        c[2 + j] = k_j.k_j + 2 sigma_j p.k_j,
+//        c[2 + N + j] = k_j.k_j - 2 sigma_j p'.k_j,
+//        c[2 + 2N + a N + b] = 2 sigma_a sigma_b k_a.k_b (a < b),
+//        c[2 + 2N + N N] = 0,
+//      so that D_T = Q_T^2 - m^2 with Q_T = p + sum_{j in T} sigma_j k_j is
+//        c[0] + sum_{j in T} c[2 + j] + sum_{a<b in T} c[2 + 2N + a N + b],
+//      and, with Q_T = p' - sum_{j in U} sigma_j k_j (U the complement of T),
+//        c[1] + sum_{j in U} c[2 + N + j] + sum_{a<b in U} c[2 + 2N + a N + b].
+// Returns after a team barrier, with w and c complete.
+template <int N, int TEAM>
+__device__ __forceinline__ void setup_invariants(int lane, double mass, const double* s_mom, double* s_w) {
+  constexpr int NP = 2 + 3 * N + N * (N - 1) / 2;
+  constexpr int NC = 2 + 2 * N + N * (N - 1) / 2;
+  for (int it = lane; it < NP; it += TEAM) {
+    int a, b;
+    if (it < 2) {
+      a = b = it == 0 ? 0 : 2;
+    } else if (it < 2 + N) {
+      a = b = photon_slot_of(it - 2);
+    } else if (it < 2 + 3 * N) {
+      a = it < 2 + 2 * N ? 0 : 2;
+      b = photon_slot_of((it - 2) % N);
+    } else {
+      int r = it - 2 - 3 * N, i = 0;
+      while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
+      a = photon_slot_of(i);
+      b = photon_slot_of(i + 1 + r);
+    }
+    s_w[it] = mdot(s_mom + 4 * a, s_mom + 4 * b);
+  }
+  team_sync<TEAM>();
+  double* c = s_w + NP;
+  for (int it = lane; it < NC; it += TEAM) {
+    double f, x, y;
+    int dst = it;
+    if (it < 2) {
+      f = -mass; x = mass; y = s_w[it];
+    } else if (it < 2 + 2 * N) {
+      const int j = (it - 2) % N;
+      const bool out = it >= 2 + N;
+      f = (j == 0) != out ? 2.0 : -2.0;   // in: 2 sigma_j; out: -2 sigma_j
+      x = s_w[(out ? 2 + 2 * N : 2 + N) + j];
+      y = s_w[2 + j];
+    } else {
+      int r = it - 2 - 2 * N, i = 0;
+      const int rank = r;
+      while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
+      f = i == 0 ? -2.0 : 2.0;            // 2 sigma_i sigma_j (j >= 1)
+      x = s_w[2 + 3 * N + rank];
+      y = 0.0;
+      dst = 2 + 2 * N + i * N + (i + 1 + r);
+    }
+    c[dst] = fma(f, x, y);
+  }
+  if (lane == 0) c[2 + 2 * N + N * N] = 0.0;
+  team_sync<TEAM>();
+}
+
 // Per point: momenta into shared memory, the propagator table (a3) and the
 // external states (a2).
 //
 // FP64 form: Q_T = p + sum_{j in T} sigma_j k_j (sigma = +1 for the incoming
 // photon, -1 for the outgoing ones) and D_T = Q_T^2 - m^2, both in FP64.
 //
-// Mixed form: the same D_T, in FP64, but summed from Lorentz invariants
-// computed once per point,
+// Mixed form: the same D_T, in FP64, but summed from the Lorentz invariants
+// and their signed combinations computed once per point (setup_invariants),
 //   D_T = (p^2 - m^2) + sum_{j in T} (k_j^2 + 2 sigma_j p.k_j)
 //         + sum_{i<j in T} 2 sigma_i sigma_j k_i.k_j,
 // or, for |T| > n/2, from the outgoing electron's side with the complement,
@@ -287,54 +359,68 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
       for (int c = 0; c < 5; ++c) d[c] = P[c];
     }
   } else {
-    // ---- a3, mixed: the invariants [p^2-m^2, p'^2-m^2, in-side singles,
-    // out-side singles, pairs (N x N, i < j used)]
-    constexpr int NPAIR = N * (N - 1) / 2;
-    const double* pin = s_mom;
-    const double* pout = s_mom + 8;
-    for (int it = lane; it < 2 + 2 * N + NPAIR; it += TEAM) {
-      if (it < 2) {
-        const double* q = it == 0 ? pin : pout;
-        s_w[it] = fma(-p.mass, p.mass, mdot(q, q));
-      } else if (it < 2 + 2 * N) {
-        const int j = (it - 2) % N;
-        const bool out = it >= 2 + N;
-        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
-        const double two_sigma = (j == 0) != out ? 2.0 : -2.0;   // in: 2 sigma_j; out: -2 sigma_j
-        s_w[it] = fma(two_sigma, mdot(out ? pout : pin, kj), mdot(kj, kj));
-      } else {
-        int r = it - 2 - 2 * N, i = 0;
-        while (r >= N - 1 - i) { r -= N - 1 - i; ++i; }
-        const int j = i + 1 + r;
-        const double* ki = s_mom + 4 * (i == 0 ? 1 : i + 2);
-        const double* kj = s_mom + 4 * (j == 0 ? 1 : j + 2);
-        const double two_ss = i == 0 ? -2.0 : 2.0;   // 2 sigma_i sigma_j (j >= 1)
-        s_w[2 + 2 * N + i * N + j] = two_ss * mdot(ki, kj);
-      }
-    }
-    team_sync<TEAM>();
-    for (int mask = lane; mask < NSUB; mask += TEAM) {
+    // ---- a3, mixed: the invariants and their signed combinations c, then
+    // the subsets of this lane, a fixed number per lane (two at a time, so
+    // that their FP64 chains interleave) and the same instructions on every lane:
+    // the U photons summed (at most N / 2) read the zero slot where U has
+    // fewer, and D_T is summed in four interleaved partial sums (depth 3 for
+    // three photons rather than a chain of six additions)
+    setup_invariants<N, TEAM>(lane, p.mass, s_mom, s_w);
+    const double* cmb = s_w + (2 + 3 * N + N * (N - 1) / 2);
+    constexpr int UMAX = N / 2;
+    constexpr int NT = 1 + UMAX + UMAX * (UMAX - 1) / 2;   // terms of a denominator
+    static_assert(NT >= 1, "at least the electron's own term");
+    constexpr int ZERO = 2 + 2 * N + N * N;
+    constexpr int ITER = (NSUB + TEAM - 1) / TEAM;
+#pragma unroll (ITER < 2 ? ITER : 2)
+    for (int t = 0; t < ITER; ++t) {
+      const int mask = lane + t * TEAM;
+      if (NSUB % TEAM != 0 && mask >= NSUB) break;
       float* d = reinterpret_cast<float*>(s_q) + mask * 5;
-      if (mask == 0 || mask == (int)ALL) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) d[c] = 0.f;
-        continue;
-      }
       const bool out = 2 * __popc(mask) > N;
       const unsigned U = out ? ALL & ~(unsigned)mask : (unsigned)mask;
-      double D = s_w[out ? 1 : 0];
+      int js[UMAX];
+      unsigned rest = U;
+#pragma unroll
+      for (int i = 0; i < UMAX; ++i) {
+        js[i] = rest ? __ffs(rest) - 1 : -1;
+        rest &= rest - 1;
+      }
+      const int so = out ? 2 + N : 2;
+      // the NT terms in NA interleaved partial sums, then added as a tree
+      constexpr int NA = NT < 4 ? NT : 4;
+      double acc[NA];
+      acc[0] = cmb[out ? 1 : 0];
+      int q = 1;
+      auto add = [&](double x) {
+        if (q < NA) acc[q] = x; else acc[q % NA] += x;
+        ++q;
+      };
+#pragma unroll
+      for (int i = 0; i < UMAX; ++i) add(cmb[js[i] < 0 ? ZERO : so + js[i]]);
+#pragma unroll
+      for (int i = 0; i < UMAX; ++i)
+#pragma unroll
+        for (int l = i + 1; l < UMAX; ++l)   // js[l] >= 0 implies js[i] >= 0
+          add(cmb[js[l] < 0 ? ZERO : 2 + 2 * N + js[i] * N + js[l]]);
+#pragma unroll
+      for (int w = 1; w < NA; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < NA; i += 2 * w) acc[i] += acc[i + w];
+      const double D = acc[0];
+      // the numerator in float-float: q + sum_{j in U} tau_j k_j (tau_j =
+      // sigma_j on the incoming side, -sigma_j on the outgoing side)
       float qh[4], ql[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         qh[c] = s_momf[(out ? 8 : 0) + c];
         ql[c] = s_momf[NS * 4 + (out ? 8 : 0) + c];
       }
-      for (unsigned a = U; a; a &= a - 1) {
-        const int j = __ffs(a) - 1;
-        D += s_w[2 + (out ? N : 0) + j];
-        for (unsigned b = a & (a - 1); b; b &= b - 1) D += s_w[2 + 2 * N + j * N + (__ffs(b) - 1)];
+#pragma unroll 1
+      for (int i = 0; i < UMAX; ++i) {
+        const int j = js[i] < 0 ? 0 : js[i];
         const int o = 4 * (j == 0 ? 1 : j + 2);
-        const float sg = (j == 0) != out ? 1.f : -1.f;
+        const float sg = js[i] < 0 ? 0.f : ((j == 0) != out ? 1.f : -1.f);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float sum, err;
@@ -343,7 +429,8 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
           ql[c] = __fadd_rn(ql[c], __fadd_rn(err, sg * s_momf[NS * 4 + o + c]));
         }
       }
-      const float inv = 1.0f / (float)D;
+      const bool used = mask != 0 && mask != (int)ALL;
+      const float inv = used ? 1.0f / (float)D : 0.0f;
       const float m = (float)p.mass;
       // Q0 -+ m: the high part first (exact where Q0 is close to m)
       d[0] = __fadd_rn(__fadd_rn(qh[0], m), ql[0]) * inv;
@@ -354,8 +441,29 @@ __device__ __forceinline__ void point_setup(const KParams& p, int lane, long lon
     }
   }
   // ---- a2: external states u(p, +-), ubar(p', +-), eps_j(pol 1, 2) in
-  // the working precision
+  // the working precision; the mixed form's from the float-float momenta
+  // (E +- m as float-float sums rounded once), with no FP64 instruction
   for (int it = lane; it < 4 + 2 * N; it += TEAM) {
+    if constexpr (INV) {
+      if (it < 4) {
+        const int side = it >> 1, e = it & 1;
+        const float* h = s_momf + (side ? 8 : 0);
+        const float* l = s_momf + NS * 4 + (side ? 8 : 0);
+        const float mf = (float)p.mass;
+        float sp[8];
+        make_spinor_core<float>(h[1], h[2], h[3], __fadd_rn(__fadd_rn(h[0], mf), l[0]),
+                                __fadd_rn(__fsub_rn(h[0], mf), l[0]), e, side == 1, sp);
+        store8(reinterpret_cast<float*>(s_spin) + (side * 2 + e) * 8, sp);
+      } else {
+        const int j = (it - 4) >> 1, pb = (it - 4) & 1;
+        const float* h = s_momf + 4 * photon_slot_of(j);
+        float ev[3];
+        make_pol_core<float>(h[1], h[2], h[3], pb, ev);
+        float* d = reinterpret_cast<float*>(s_eps) + (j * 2 + pb) * 4;
+        d[0] = ev[0]; d[1] = ev[1]; d[2] = ev[2]; d[3] = 0.f;
+      }
+      continue;
+    }
     if (it < 4) {
       const int side = it >> 1, e = it & 1;
       Real s[8];

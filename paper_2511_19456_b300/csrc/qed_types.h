@@ -18,10 +18,12 @@ struct TeamLayout {
   int mom, q, eps, spin, red, w, momf, cur, bytes;
 };
 
-// Mixed form's set-up scratch: FP64 Lorentz invariants from which every
-// denominator is summed (see point_setup), and the momenta as float-float
-// pairs.
-QED_HD int n_invariants(int n) { return 2 + 2 * n + n * n; }
+// Mixed form's set-up scratch (see setup_invariants): the FP64 Minkowski
+// products of the point's momenta, the signed combinations from which every
+// denominator is summed (pairs at a square index) and a zero slot; then the
+// momenta as float-float pairs.
+QED_HD int n_products(int n) { return 2 + 3 * n + n * (n - 1) / 2; }
+QED_HD int n_invariants(int n) { return n_products(n) + 2 + 2 * n + n * n + 1; }
 
 QED_HD int align16(int x) { return (x + 15) & ~15; }
 
