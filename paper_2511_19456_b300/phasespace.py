@@ -229,6 +229,9 @@ WORKLOADS = {
     "compton_k1": dict(k=1, n_points=65536, omega=1.0, seed=1, summed=True, hel=None),
     # e- gamma -> e- + 4 gamma, 120 diagrams, 128 states summed, omega = 4
     "compton_k4": dict(k=4, n_points=1 << 20, omega=4.0, seed=2, summed=True, hel=None),
+    # e- gamma -> e- + 5 gamma, 720 diagrams, 256 states summed, omega = 6:
+    # the kind of request that carries most of the batched stream's work
+    "compton_k5": dict(k=5, n_points=1 << 19, omega=6.0, seed=6, summed=True, hel=None),
     # e- gamma -> e- + 6 gamma, 5040 diagrams, one fixed state, omega = 8
     "compton_k6_fixed": dict(k=6, n_points=262144, omega=8.0, seed=3, summed=False, hel=K6_HEL),
     # e- gamma -> e- + 7 gamma, 40320 diagrams, 1024 states summed, omega = 10
