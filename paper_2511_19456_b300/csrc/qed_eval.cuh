@@ -3,7 +3,7 @@
 // kernels.
 #pragma once
 
-#include "qed_team.cuh"
+#include "qed_spec.cuh"
 
 namespace qed {
 
@@ -24,8 +24,9 @@ __device__ __forceinline__ void eval_point(const KParams& p, long long pt, bool 
   double* s_red = reinterpret_cast<double*>(base + L.red);
   Real* s_cur = reinterpret_cast<Real*>(base + L.cur);
 
-  point_setup<K, Real, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin,
-                             reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
+  spec::team_setup<K, Real, TEAM, SUMMED>(p, lane, pt, s_mom, s_q, s_eps, s_spin,
+                                          reinterpret_cast<double*>(base + L.w),
+                                          reinterpret_cast<float*>(base + L.momf));
 
   // ---- a4/a5: currents kept for the whole point
   for (int ph = 0; ph < p.n_stored_phases; ++ph) {

@@ -8,7 +8,7 @@
 // factorially.
 #include <cuda_runtime.h>
 
-#include "qed_team.cuh"
+#include "qed_spec.cuh"
 
 namespace qed {
 
@@ -137,17 +137,19 @@ __device__ __forceinline__ void run_sum_phase(const Phase& ph, int lane, const K
 }  // namespace
 
 // Block: one team when TEAM > 32, else 128 threads; FP64 instances may use up
-// to about 96 registers per thread, FP32 ones 64.
+// to about 96 registers per thread, FP32 ones 64 (72 with the FP64-light
+// set-up of spin-summed k <= 4).
 template <typename Real, int TEAM>
 constexpr int rw_block() { return TEAM > 32 ? TEAM : 128; }
-template <typename Real, int TEAM>
+template <typename Real, int TEAM, int K, bool SUMMED>
 constexpr int rw_min_blocks() {
-  constexpr int b = 65536 / (rw_block<Real, TEAM>() * (sizeof(Real) == 8 ? 96 : 64));
+  constexpr int regs = sizeof(Real) == 8 ? 96 : (SUMMED && K <= 4 ? 72 : 64);
+  constexpr int b = 65536 / (rw_block<Real, TEAM>() * regs);
   return b < 1 ? 1 : b;
 }
 
 template <int K, bool SUMMED, typename Real, int TEAM>
-__global__ void __launch_bounds__(rw_block<Real, TEAM>(), rw_min_blocks<Real, TEAM>())
+__global__ void __launch_bounds__(rw_block<Real, TEAM>(), rw_min_blocks<Real, TEAM, K, SUMMED>())
 qed_rw_kernel(const KParams p) {
   constexpr int N = K + 1;
   constexpr int H = (N + 1) / 2;
@@ -175,8 +177,9 @@ qed_rw_kernel(const KParams p) {
   for (long long pt0 = (long long)blockIdx.x * tpc; pt0 < p.n; pt0 += (long long)gridDim.x * tpc) {
     const long long pt = pt0 + team;
     const bool valid = pt < p.n;
-    point_setup<K, Real, TEAM>(p, lane, valid ? pt : p.n - 1, s_mom, s_q, s_eps, s_spin,
-                               reinterpret_cast<double*>(base + L.w), reinterpret_cast<float*>(base + L.momf));
+    spec::team_setup<K, Real, TEAM, SUMMED>(p, lane, valid ? pt : p.n - 1, s_mom, s_q, s_eps, s_spin,
+                                            reinterpret_cast<double*>(base + L.w),
+                                            reinterpret_cast<float*>(base + L.momf));
     for (int ph = 0; ph < p.n_stored_phases; ++ph) {
       run_sum_phase<TEAM, SUMMED, Real>(ld_phase(p.phases + ph), lane, p, s_q, s_eps, s_spin, s_cur);
       team_sync<TEAM>();

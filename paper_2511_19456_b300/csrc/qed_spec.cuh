@@ -123,7 +123,7 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
   constexpr unsigned ALL = (1u << N) - 1;
   constexpr int NPROD = 2 + 3 * N + N * (N - 1) / 2;
   constexpr int ZERO = 2 + 2 * N + N * N;   // the zero slot of the combinations
-  static_assert((1 << N) == TEAM, "one lane per photon subset");
+  static_assert((1 << N) <= TEAM, "a lane for every photon subset");
   static_assert(N / 2 <= 2, "at most two photons per denominator");
   // 1. momenta (FP64) and their float-float split
   for (int i = lane; i < NC; i += TEAM) {
@@ -137,8 +137,8 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
   // 2. the invariants and their combinations c
   setup_invariants<N, TEAM>(lane, p.mass, s_mom, s_w);
   const double* cmb = s_w + NPROD;
-  // 3. the subset of this lane
-  {
+  // 3. the subset of this lane (lanes past the 2^n subsets have none)
+  if (lane < (1 << N)) {
     const unsigned T = (unsigned)lane;
     float* d = s_q + T * 5;
     const bool out = 2 * __popc(T) > N;
@@ -201,6 +201,18 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
     }
   }
   team_sync<TEAM>();
+}
+
+// The set-up of a team (a1-a3 and the external states): the FP64-light form
+// above for spin-summed mixed teams, whose lanes cover every photon subset
+// (k <= 4), else point_setup.
+template <int K, typename Real, int TEAM, bool SUMMED>
+__device__ __forceinline__ void team_setup(const KParams& p, int lane, long long pt, double* s_mom, Real* s_q,
+                                           Real* s_eps, Real* s_spin, double* s_w, float* s_momf) {
+  if constexpr (SUMMED && sizeof(Real) == 4 && K <= 4 && (1 << (K + 1)) <= TEAM)
+    setup_f32<K, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin, s_w, s_momf);
+  else
+    point_setup<K, Real, TEAM>(p, lane, pt, s_mom, s_q, s_eps, s_spin, s_w, s_momf);
 }
 
 // One vertex item (task V), optionally followed by its propagation (task S1,
