@@ -18,6 +18,9 @@ namespace qed {
 // ------------------------------------------------------------ U: states
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+// 1/sqrt(x): CUDA's rsqrt (1 ulp in FP64) and rsqrtf (2 ulp)
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 
 // Helicity spinor u(p, h) in precision T:
 // u = (sqrt(E+m) chi, h sqrt(E-m) chi), chi_+ = (|p|+pz, px + i py)/N,
@@ -27,7 +30,9 @@ __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 // (px^2 + py^2)/(|p| - pz) when pz < 0 (the same quantity without the
 // cancellation near the -z axis).  make_spinor_core takes px, py, pz and
 // E + m, E - m already in precision T; make_spinor forms them from the FP64
-// momentum (E +- m in FP64).
+// momentum (E +- m in FP64).  The 1/N of both helicities is one reciprocal
+// square root, so that the lanes of a warp that build the two helicities
+// run the same instructions.
 template <typename T>
 __device__ __forceinline__ void make_spinor_core(T px, T py, T pz, T epm, T emm, int hbit, bool bar, T out[8]) {
   const T pt2 = px * px + py * py;
@@ -42,9 +47,12 @@ __device__ __forceinline__ void make_spinor_core(T px, T py, T pz, T epm, T emm,
     if (apz == (T)0) {
       c0r = hbit ? (T)-1 : (T)0; c0i = (T)0; c1r = hbit ? (T)0 : (T)1; c1i = (T)0;
     } else {
-      const T nrm = sqrt_t((T)2 * ap * apz);
-      if (!hbit) { c0r = apz / nrm; c0i = (T)0; c1r = px / nrm; c1i = py / nrm; }
-      else       { c0r = -px / nrm; c0i = py / nrm; c1r = apz / nrm; c1i = (T)0; }
+      const T inv = rsqrt_t((T)2 * ap * apz);
+      const T za = apz * inv, zx = px * inv, zy = py * inv;
+      c0r = hbit ? -zx : za;
+      c0i = hbit ? zy : (T)0;
+      c1r = hbit ? za : zx;
+      c1i = hbit ? (T)0 : zy;
     }
   }
   const T a = sqrt_t(epm);
@@ -67,7 +75,10 @@ __device__ __forceinline__ void make_spinor(const double* p, int hbit, double m,
 }
 
 // Real linear polarisation 3-vector (eps^0 = 0) of a photon with momentum
-// components (kx, ky, kz) in precision T.
+// components (kx, ky, kz) in precision T:
+//   eps_1 = (kx kz, ky kz, -kt^2) / (|k| kt),  eps_2 = (-ky, kx, 0) / kt,
+// kt^2 = kx^2 + ky^2, with 1/kt and 1/|k| as reciprocal square roots (both
+// polarisations run the same instructions).
 template <typename T>
 __device__ __forceinline__ void make_pol_core(T kx, T ky, T kz, int pbit, T e[3]) {
   const T kt2 = kx * kx + ky * ky;
@@ -75,13 +86,11 @@ __device__ __forceinline__ void make_pol_core(T kx, T ky, T kz, int pbit, T e[3]
     e[0] = pbit ? (T)0 : (T)1; e[1] = pbit ? (T)1 : (T)0; e[2] = (T)0;
     return;
   }
-  const T kt = sqrt_t(kt2);
-  if (!pbit) {
-    const T den = sqrt_t(kt2 + kz * kz) * kt;
-    e[0] = kx * kz / den; e[1] = ky * kz / den; e[2] = -kt2 / den;
-  } else {
-    e[0] = -ky / kt; e[1] = kx / kt; e[2] = (T)0;
-  }
+  const T ikt = rsqrt_t(kt2);
+  const T inv = rsqrt_t(kt2 + kz * kz) * ikt;   // 1 / (|k| kt)
+  e[0] = pbit ? -ky * ikt : kx * kz * inv;
+  e[1] = pbit ? kx * ikt : ky * kz * inv;
+  e[2] = pbit ? (T)0 : -kt2 * inv;
 }
 // ... of a photon with FP64 momentum k.
 template <typename T>
