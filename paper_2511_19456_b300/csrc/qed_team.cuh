@@ -504,10 +504,10 @@ __device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab
   constexpr bool ONE_STEP = NL * NR <= 12;
     if constexpr (SUMMED && sizeof(Real) == 4 && !ONE_STEP) {
       // mixed, more than 12 diagrams per set: packed FP32 FMAs (two per
-      // instruction).  The BC right leaves of a block stay in registers as
-      // (re, im) pairs; each left leaf variant is loaded once per block and
-      // broadcast to (re, re) and (im, im) pairs:
-      //   A += (lr, lr) * (rr, ri),  B += (li, li) * (rr, ri),
+      // instruction).  The BC right leaves of a block stay in registers,
+      // broadcast once per block to (re, re) and (im, im) pairs; each left
+      // leaf variant is loaded once per block as its natural (re, im) pairs:
+      //   A += (rr, rr) * (lr, li),  B += (ri, ri) * (lr, li),
       //   Re M = A.x - B.y,  Im M = A.y + B.x,
       // with A starting from minus the state's compensation; the GA x BC
       // diagrams of a block are one compensated step per state, as in the
@@ -518,7 +518,7 @@ __device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab
       const int vl = ((int)(tv & 0xffu) << 1) + (ES >= 2 ? (ep & 1) : 0);
       const int vr = ((int)(tv >> 8) << 1) + (ES >= 4 ? (ep >> 1) : 0);
       for (int b0 = 0; b0 < NR; b0 += BC) {
-        float2 rp[BC][NSO][4];
+        float2 rr[BC][NSO][4], ri[BC][NSO][4];
 #pragma unroll
         for (int bb = 0; bb < BC; ++bb)
 #pragma unroll
@@ -526,7 +526,10 @@ __device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab
             float x[8];
             load_cur(s_cur, se.leaf_r + (b0 + bb) * NVR, NVR, vr + so, x);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) rp[bb][so][q] = make_float2(x[2 * q], x[2 * q + 1]);
+            for (int q = 0; q < 4; ++q) {
+              rr[bb][so][q] = make_float2(x[2 * q], x[2 * q]);
+              ri[bb][so][q] = make_float2(x[2 * q + 1], x[2 * q + 1]);
+            }
           }
         for (int a0 = 0; a0 < NL; a0 += GA) {
           float2 A[NSI][NSO], B[NSI][NSO];
@@ -543,20 +546,17 @@ __device__ __forceinline__ void join_set(const SetEntry& se, const uint16_t* tab
             for (int si = 0; si < NSI; ++si) {
               float x[8];
               load_cur(s_cur, se.leaf_l + (a0 + ga) * NVL, NVL, vl + si, x);
-              float2 lr[4], li[4];
+              float2 l[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                lr[q] = make_float2(x[2 * q], x[2 * q]);
-                li[q] = make_float2(x[2 * q + 1], x[2 * q + 1]);
-              }
+              for (int q = 0; q < 4; ++q) l[q] = make_float2(x[2 * q], x[2 * q + 1]);
 #pragma unroll
               for (int so = 0; so < NSO; ++so)
 #pragma unroll
                 for (int bb = 0; bb < BC; ++bb)
 #pragma unroll
                   for (int q = 0; q < 4; ++q) {
-                    A[si][so] = __ffma2_rn(lr[q], rp[bb][so][q], A[si][so]);
-                    B[si][so] = __ffma2_rn(li[q], rp[bb][so][q], B[si][so]);
+                    A[si][so] = __ffma2_rn(rr[bb][so][q], l[q], A[si][so]);
+                    B[si][so] = __ffma2_rn(ri[bb][so][q], l[q], B[si][so]);
                   }
             }
 #pragma unroll
