@@ -376,8 +376,9 @@ void qed_batch_destroy(qed_batch_t batch);
  *     cudaMalloc/cudaFree implies.
  *
  * Behaviour:
- *   - It runs the same persistent kernel as qed_batch_eval on the same kinds
- *     of request: spin-summed plans, k <= 5, all of one precision.
+ *   - It runs the same persistent kernel as qed_batch_eval in a new batch's
+ *     form (QED_KERNEL_SPECIALISED), with 128-thread blocks, on the same
+ *     kinds of request: spin-summed plans, k <= 5, all of one precision.
  *   - The counter, request table and work items live in a static device
  *     array of about 1.53 MiB, which every GPU that loads the library holds
  *     until the process exits.

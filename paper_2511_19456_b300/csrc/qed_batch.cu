@@ -44,6 +44,25 @@ struct qed_batch_s {
   cudaGraphExec_t exec = nullptr;
 };
 
+namespace qed {
+
+BatchFn batch_fn(bool mixed, int form) {
+  if (form == QED_KERNEL_SPECIALISED) return batch_spec_kernel(mixed);
+  return mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>;
+}
+
+// Shared memory per team of a request's points in a form: the specialised
+// kernel's own layout where it has one, else the plan's table kernel layout.
+int team_bytes_of(const qed_plan_s* P, int form) {
+  if (form == QED_KERNEL_SPECIALISED) {
+    const SpecKernel sk = spec_forward_kernel(P->k, P->prec == QED_MIXED);
+    if (sk.fn) return sk.team_bytes;
+  }
+  return P->team_bytes;
+}
+
+}  // namespace qed
+
 namespace {
 
 constexpr int kMaxBatchK = 5;
@@ -63,21 +82,6 @@ void free_batch(qed_batch_s* b) {
   cudaFree(b->d_counter);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
-}
-
-BatchFn batch_fn(bool mixed, int form) {
-  if (form == QED_KERNEL_SPECIALISED) return batch_spec_kernel(mixed);
-  return mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>;
-}
-
-// Shared memory per team of a request's points in a form: the specialised
-// kernel's own layout where it has one, else the plan's table kernel layout.
-int team_bytes_of(const qed_plan_s* P, int form) {
-  if (form == QED_KERNEL_SPECIALISED) {
-    const SpecKernel sk = spec_forward_kernel(P->k, P->prec == QED_MIXED);
-    if (sk.fn) return sk.team_bytes;
-  }
-  return P->team_bytes;
 }
 
 // Work list, launch shape and graph for the current (block, work_target).

@@ -6,6 +6,8 @@
 
 #include "qed_eval.cuh"
 
+struct qed_plan_s;
+
 namespace qed {
 
 struct BatchItem {
@@ -56,6 +58,13 @@ using BatchFn = void (*)(const BatchDesc*, const BatchItem*, int, unsigned*);
 // straight-line forward kernels): the same work-item loop, with the
 // straight-line point evaluation of every k.
 BatchFn batch_spec_kernel(bool mixed);
+
+// The batched kernel of a form (QED_KERNEL_TABLE or QED_KERNEL_SPECIALISED),
+// and the shared memory per team of a plan's points in that form (the
+// specialised kernel's own layout where it has one, else the plan's table
+// layout); both defined in qed_batch.cu.
+BatchFn batch_fn(bool mixed, int form);
+int team_bytes_of(const qed_plan_s* P, int form);
 
 // The largest dynamic shared memory a launch of fn may ask for: the device's
 // opt-in maximum less the kernel's static shared memory.

@@ -5,7 +5,8 @@
 // its own memory pool and forbids foreign cudaMalloc calls. Another is a
 // latency-critical serving loop, where the implicit device synchronisation of
 // cudaMalloc/cudaFree is not acceptable. For them this entry point runs the
-// same persistent batched kernel as qed_batch_eval, but its scratch (the work
+// same persistent batched kernel as qed_batch_eval in its default
+// (straight-line) form, but its scratch (the work
 // counter, the request table and the work items) lives in a file-scope static
 // device array of fixed size. Every GPU that loads the library holds that
 // array until the process exits.
@@ -65,7 +66,8 @@ extern "C" qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
-  auto fn = mixed ? qed_batch_kernel<float> : qed_batch_kernel<double>;
+  // the straight-line form, qed_batch_eval's default
+  const BatchFn fn = batch_fn(mixed, QED_KERNEL_SPECIALISED);
   int dev_smem = 0, sms = 0;
   e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -83,7 +85,7 @@ extern "C" qed_status qed_batch_eval_static(const qed_plan_t* plans, int n_req, 
   size_t smem = 0;
   for (int r = 0; r < n_req; ++r) {
     const int team = 1 << (plans[r]->k + 1);
-    smem = std::max(smem, (size_t)(kBlock / team) * plans[r]->team_bytes);
+    smem = std::max(smem, (size_t)(kBlock / team) * team_bytes_of(plans[r], QED_KERNEL_SPECIALISED));
   }
   if (smem + 64 > (size_t)dev_smem) return QED_EUNSUPPORTED;
   double target = 4e8;
