@@ -30,9 +30,10 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 // (px^2 + py^2)/(|p| - pz) when pz < 0 (the same quantity without the
 // cancellation near the -z axis).  make_spinor_core takes px, py, pz and
 // E + m, E - m already in precision T; make_spinor forms them from the FP64
-// momentum (E +- m in FP64).  The 1/N of both helicities is one reciprocal
-// square root, so that the lanes of a warp that build the two helicities
-// run the same instructions.
+// momentum (E +- m in FP64).  Both helicities take the same three quotients
+// by N (in FP64 through one reciprocal square root), so that the lanes of a
+// warp that build the two helicities run the same instructions; in FP32 the
+// quotients are IEEE divisions by the rounded N.
 template <typename T>
 __device__ __forceinline__ void make_spinor_core(T px, T py, T pz, T epm, T emm, int hbit, bool bar, T out[8]) {
   const T pt2 = px * px + py * py;
@@ -47,8 +48,14 @@ __device__ __forceinline__ void make_spinor_core(T px, T py, T pz, T epm, T emm,
     if (apz == (T)0) {
       c0r = hbit ? (T)-1 : (T)0; c0i = (T)0; c1r = hbit ? (T)0 : (T)1; c1i = (T)0;
     } else {
-      const T inv = rsqrt_t((T)2 * ap * apz);
-      const T za = apz * inv, zx = px * inv, zy = py * inv;
+      T za, zx, zy;
+      if constexpr (sizeof(T) == 8) {
+        const T inv = rsqrt_t((T)2 * ap * apz);
+        za = apz * inv; zx = px * inv; zy = py * inv;
+      } else {
+        const T nrm = sqrt_t((T)2 * ap * apz);
+        za = apz / nrm; zx = px / nrm; zy = py / nrm;
+      }
       c0r = hbit ? -zx : za;
       c0i = hbit ? zy : (T)0;
       c1r = hbit ? za : zx;
@@ -77,8 +84,9 @@ __device__ __forceinline__ void make_spinor(const double* p, int hbit, double m,
 // Real linear polarisation 3-vector (eps^0 = 0) of a photon with momentum
 // components (kx, ky, kz) in precision T:
 //   eps_1 = (kx kz, ky kz, -kt^2) / (|k| kt),  eps_2 = (-ky, kx, 0) / kt,
-// kt^2 = kx^2 + ky^2, with 1/kt and 1/|k| as reciprocal square roots (both
-// polarisations run the same instructions).
+// kt^2 = kx^2 + ky^2; both polarisations run the same instructions (in FP64
+// 1/kt and 1/|k| as reciprocal square roots; in FP32 IEEE divisions by the
+// rounded kt and |k| kt).
 template <typename T>
 __device__ __forceinline__ void make_pol_core(T kx, T ky, T kz, int pbit, T e[3]) {
   const T kt2 = kx * kx + ky * ky;
@@ -86,11 +94,21 @@ __device__ __forceinline__ void make_pol_core(T kx, T ky, T kz, int pbit, T e[3]
     e[0] = pbit ? (T)0 : (T)1; e[1] = pbit ? (T)1 : (T)0; e[2] = (T)0;
     return;
   }
-  const T ikt = rsqrt_t(kt2);
-  const T inv = rsqrt_t(kt2 + kz * kz) * ikt;   // 1 / (|k| kt)
-  e[0] = pbit ? -ky * ikt : kx * kz * inv;
-  e[1] = pbit ? kx * ikt : ky * kz * inv;
-  e[2] = pbit ? (T)0 : -kt2 * inv;
+  T e1[3], e2[2];
+  if constexpr (sizeof(T) == 8) {
+    const T ikt = rsqrt_t(kt2);
+    const T inv = rsqrt_t(kt2 + kz * kz) * ikt;   // 1 / (|k| kt)
+    e1[0] = kx * kz * inv; e1[1] = ky * kz * inv; e1[2] = -kt2 * inv;
+    e2[0] = -ky * ikt; e2[1] = kx * ikt;
+  } else {
+    const T kt = sqrt_t(kt2);
+    const T den = sqrt_t(kt2 + kz * kz) * kt;
+    e1[0] = kx * kz / den; e1[1] = ky * kz / den; e1[2] = -kt2 / den;
+    e2[0] = -ky / kt; e2[1] = kx / kt;
+  }
+  e[0] = pbit ? e2[0] : e1[0];
+  e[1] = pbit ? e2[1] : e1[1];
+  e[2] = pbit ? (T)0 : e1[2];
 }
 // ... of a photon with FP64 momentum k.
 template <typename T>
@@ -220,6 +238,17 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// E + m and E - m from the float-float energy (hi, lo) and the FP32 mass:
+// TwoSum of the high parts, then the low parts added to its error, so that
+// each is rounded about once (where E is close to m, hi - m is exact).
+__device__ __forceinline__ void e_pm_m_ff(float hi, float lo, float m, float& epm, float& emm) {
+  float s, e;
+  two_sum_f(hi, m, s, e);
+  epm = __fadd_rn(s, __fadd_rn(e, lo));
+  two_sum_f(hi, -m, s, e);
+  emm = __fadd_rn(s, __fadd_rn(e, lo));
 }
 
 // Adds (hi - c)^2 to the float-float accumulator (acc_hi, acc_lo); hi - c is a

@@ -188,8 +188,9 @@ __device__ __forceinline__ void setup_f32(const KParams& p, int lane, long long 
       const float* l = s_momf + NC + (side ? 8 : 0);
       const float mf = (float)p.mass;
       float sp[8];
-      make_spinor_core<float>(h[1], h[2], h[3], __fadd_rn(__fadd_rn(h[0], mf), l[0]),
-                              __fadd_rn(__fsub_rn(h[0], mf), l[0]), e, side == 1, sp);
+      float epm, emm;
+      e_pm_m_ff(h[0], l[0], mf, epm, emm);
+      make_spinor_core<float>(h[1], h[2], h[3], epm, emm, e, side == 1, sp);
       store8(s_spin + (side * 2 + e) * 8, sp);
     } else {
       const int j = (it - 4) >> 1, pb = (it - 4) & 1;
