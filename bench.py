@@ -42,14 +42,14 @@ PEAK_FP64_TFLOPS = 1.25
 # profiles/traffic.json is reported only for the version it was measured on.
 # FWD: the table-driven kernel (qed_fwd.cu); SPEC: the straight-line
 # specialised kernel (the kernel version its generator writes).
-FWD_KERNEL_VERSION = "fwd-7"
-SPEC_KERNEL_VERSION = "spec-5"
+FWD_KERNEL_VERSION = "fwd-8"
+SPEC_KERNEL_VERSION = "spec-6"
 # Mixed-precision and FP64 per-point bounds against the oracle (as the GPU
 # tests state them): 64 u32 max(kappa, 1) and max(1e-12, 64 u64 kappa).
 U32, U64 = 2.0 ** -24, 2.0 ** -53
 C_MIX = 64
 # The same for the kernel of the distributively rewritten DAG.
-RW_KERNEL_VERSION = "rw-3"
+RW_KERNEL_VERSION = "rw-4"
 
 
 def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain", form: str = "table"):

@@ -31,7 +31,7 @@ namespace {
 
 // Version of the generated kernels (layout, rounds, joins); part of the
 // benchmark's record of which kernel a counter capture belongs to.
-constexpr const char* SPEC_VERSION = "spec-5";
+constexpr const char* SPEC_VERSION = "spec-6";
 
 // One vertex (+ propagation) node of a range.  photon, src and post are C++
 // expressions: literals for the kept currents, entries of the photon set's
