@@ -69,6 +69,19 @@ def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain"
     return rec["bytes_per_launch"]
 
 
+def host_chunks(n: int) -> list:
+    """Chunk sizes of one qed_eval_host call on n points (one kernel launch
+    each): starting at an eighth of the largest chunk, doubling up to it."""
+    chunk = min(n, max(1 << 16, (n + 7) // 8))
+    size, off, out = max(min(chunk, 8192), chunk // 8), 0, []
+    while off < n:
+        m = min(size, n - off)
+        out.append(m)
+        off += m
+        size = min(chunk, 2 * size)
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -791,8 +804,7 @@ def main():
         for _ in range(args.steps):
             plan.eval_host(h_mom, h_out)
         e2e_s = (time.perf_counter() - t0) / args.steps
-        chunk = min(n, max(1 << 16, (n + 7) // 8))
-        launches += args.steps * math.ceil(n / chunk)
+        launches += args.steps * len(host_chunks(n))
         e2e_s = max_over_ranks(e2e_s, device="cuda")
         e2e = {"value": n * ws / e2e_s, "unit": "points/s",
                "h2d_bytes_per_step": int(h_mom.numel() * 8),

@@ -311,7 +311,8 @@ qed_status qed_eval_grad_ws(qed_plan_t plan, const double* d_momenta, long long 
 
 /* Not in the paper.  End-to-end form of qed_eval on HOST buffers: copies the momenta to the
  * device, evaluates and copies |M|^2 back, chunked so that copies overlap
- * the kernels.  Uses device staging owned by the plan, grown (allocated) on
+ * the kernels (the chunks grow from an eighth of the largest, max(65536,
+ * n/8) points, so that only a small first copy runs before a kernel).  Uses device staging owned by the plan, grown (allocated) on
  * the first call that needs more; synchronises `stream` before returning.
  * Calls on one plan from several host threads run one at a time (the
  * staging is the plan's); no copy outlives the call, also on error.

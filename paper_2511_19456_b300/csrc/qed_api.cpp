@@ -1108,8 +1108,12 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
   std::lock_guard<std::mutex> guard(P->stage_lock);   // the staging is the plan's
   cudaStream_t st = (cudaStream_t)stream;
   const long long stride = (long long)(P->k + 3) * 4;
-  // two staging buffers of `chunk` points each: momenta then |M|^2
+  // two staging buffers of `chunk` points each: momenta then |M|^2.  The
+  // chunks start at chunk / 8 and double up to chunk, so that only the
+  // first (small) copy runs before any kernel: each kernel covers the copy
+  // of the next, larger chunk.
   const long long chunk = std::min<long long>(n, std::max<long long>(1 << 16, (n + 7) / 8));
+  const long long first = std::max<long long>(std::min<long long>(chunk, 8192), chunk / 8);
   cudaError_t e = cudaSuccess;
   if (chunk > P->stage_cap) {
     cudaFree(P->d_stage);
@@ -1137,10 +1141,10 @@ qed_status qed_eval_host(qed_plan_t P, const double* h_momenta, long long n, dou
   e = cudaEventRecord(start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_h2d, start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_d2h, start, 0);
-  long long c = 0;
-  for (long long off = 0; off < n && e == cudaSuccess; off += chunk, ++c) {
+  long long c = 0, size = first, m = 0;
+  for (long long off = 0; off < n && e == cudaSuccess; off += m, ++c, size = std::min(chunk, 2 * size)) {
     const int b = (int)(c & 1);
-    const long long m = std::min(chunk, n - off);
+    m = std::min(size, n - off);
     if (c >= 2) e = cudaStreamWaitEvent(P->s_h2d, P->ev_k[b], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(mom_buf[b], h_momenta + off * stride, (size_t)m * stride * sizeof(double),
