@@ -45,3 +45,15 @@ def test_recorded_kernel_versions_match_the_sources():
     gen = open(os.path.join(ROOT, "paper_2511_19456_b300", "csrc", "qed_codegen.cpp")).read()
     m = re.search(r'SPEC_VERSION = "([^"]+)"', gen)
     assert m and m.group(1) == bench.SPEC_KERNEL_VERSION
+
+
+def test_host_chunks_cover_every_point_once():
+    """The chunk schedule of qed_eval_host that the bench counts launches
+    from: sizes grow from an eighth of the largest (at least 8,192 points,
+    or all of them) and double up to it, and add up to n."""
+    for n in (1, 5000, 8192, 8193, 65536, 70001, 300001, 1 << 20):
+        c = bench.host_chunks(n)
+        largest = min(n, max(1 << 16, (n + 7) // 8))
+        assert sum(c) == n and max(c) <= largest
+        assert c[0] == min(n, max(min(largest, 8192), largest // 8))
+        assert all(b <= min(largest, 2 * a) for a, b in zip(c, c[1:]))
