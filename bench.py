@@ -49,7 +49,7 @@ SPEC_KERNEL_VERSION = "spec-6"
 U32, U64 = 2.0 ** -24, 2.0 ** -53
 C_MIX = 64
 # The same for the kernel of the distributively rewritten DAG.
-RW_KERNEL_VERSION = "rw-4"
+RW_KERNEL_VERSION = "rw-5"
 
 
 def recorded_traffic(workload: str, prec: str, n_points: int, dag: str = "plain", form: str = "table"):

@@ -24,7 +24,7 @@ __device__ __forceinline__ SumInstr ld_sum_instr(const SumInstr* p) {
   return in;
 }
 
-// y += SIGN (sigma . a) x, column and row forms (SIGN = +-1), as FMA chains.
+// y += SIGN (sigma . a) x, column form (SIGN = +-1), as FMA chains.
 template <int SIGN, typename R>
 __device__ __forceinline__ void pauli_col_acc(const R a[3], const R x[4], R y[4]) {
   const R ax = SIGN * a[0], ay = SIGN * a[1], az = SIGN * a[2];
@@ -33,25 +33,11 @@ __device__ __forceinline__ void pauli_col_acc(const R a[3], const R x[4], R y[4]
   y[2] = fma(ax, x[0], fma(-ay, x[1], fma(-az, x[2], y[2])));
   y[3] = fma(ax, x[1], fma(ay, x[0], fma(-az, x[3], y[3])));
 }
-template <int SIGN, typename R>
-__device__ __forceinline__ void pauli_row_acc(const R a[3], const R x[4], R y[4]) {
-  const R ax = SIGN * a[0], ay = SIGN * a[1], az = SIGN * a[2];
-  y[0] = fma(az, x[0], fma(ax, x[2], fma(-ay, x[3], y[0])));
-  y[1] = fma(az, x[1], fma(ax, x[3], fma(ay, x[2], y[1])));
-  y[2] = fma(ax, x[0], fma(ay, x[1], fma(-az, x[2], y[2])));
-  y[3] = fma(ax, x[1], fma(-ay, x[0], fma(-az, x[3], y[3])));
-}
-
-// acc += eps/ x (side 0, column) or x eps/ (side 1, row); eps/ as in vertex_col/row.
+// acc += eps/ x (column form; eps/ as in vertex_col).
 template <typename R>
-__device__ __forceinline__ void vertex_acc(int side, const R e[3], const R x[8], R acc[8]) {
-  if (side == 0) {
-    pauli_col_acc<-1>(e, x + 4, acc);
-    pauli_col_acc<1>(e, x, acc + 4);
-  } else {
-    pauli_row_acc<1>(e, x + 4, acc);
-    pauli_row_acc<-1>(e, x, acc + 4);
-  }
+__device__ __forceinline__ void vertex_col_acc(const R e[3], const R x[8], R acc[8]) {
+  pauli_col_acc<-1>(e, x + 4, acc);
+  pauli_col_acc<1>(e, x, acc + 4);
 }
 
 __device__ __forceinline__ void load_eps(const float* p, float e[3]) {
@@ -64,10 +50,15 @@ __device__ __forceinline__ void load_eps(const double* p, double e[3]) {
 }
 
 // One node of the rewritten DAG, variant v: the sum of its NT vertex terms,
-// then the propagator of its post set.
+// then the propagator of its post set.  One code path for both sides: for a
+// real 3-vector a, x (sigma.a) = (sigma.a') x with a' = (ax, -ay, az), so a
+// row node's vertex x eps/ is the column form with eps~ = (-ex, ey, -ez) and
+// its propagation x (Q/ + m)/D the column form with Q/D replaced by
+// (-qx, qy, -qz); sign flips are exact.
 template <int NT, bool SUMMED, typename Real>
 __device__ __forceinline__ void apply_sum(const SumInstr& in, int v, const KParams& p, const Real* s_q,
                                           const Real* s_eps, const Real* s_spin, Real* s_cur) {
+  const Real sg = in.side ? (Real)-1 : (Real)1;
   Real acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = (Real)0;
@@ -92,12 +83,15 @@ __device__ __forceinline__ void apply_sum(const SumInstr& in, int v, const KPara
     }
     Real ev[3];
     load_eps(s_eps + (j * 2 + pol) * 4, ev);
-    vertex_acc(in.side, ev, x, acc);
+    ev[0] *= sg;
+    ev[2] *= sg;
+    vertex_col_acc(ev, x, acc);
   }
   if (in.post) {
     const Real* P = s_q + in.post * 5;
+    const Real Pt[5] = {P[0], P[1], sg * P[2], P[3], sg * P[4]};
     Real z[8];
-    if (in.side == 0) prop_col(P, acc, z); else prop_row(P, acc, z);
+    prop_col(Pt, acc, z);
     store_cur(s_cur, in.dst, 0, v, z);
   } else {
     store_cur(s_cur, in.dst, 0, v, acc);
@@ -119,7 +113,7 @@ __device__ __forceinline__ void run_slot(int beg, int cnt, int lg, int lane, con
 template <int TEAM, bool SUMMED, typename Real>
 __device__ __forceinline__ void run_sum_phase(const Phase& ph, int lane, const KParams& p, const Real* s_q,
                                               const Real* s_eps, const Real* s_spin, Real* s_cur) {
-#pragma unroll
+#pragma unroll 1
   for (int slot = 0; slot < 2; ++slot) {
     const int cnt = ph.cnt[slot];
     if (cnt == 0) continue;
