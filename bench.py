@@ -42,7 +42,7 @@ PEAK_FP64_TFLOPS = 1.25
 # profiles/traffic.json is reported only for the version it was measured on.
 # FWD: the table-driven kernel (qed_fwd.cu); SPEC: the straight-line
 # specialised kernel (the kernel version its generator writes).
-FWD_KERNEL_VERSION = "fwd-8"
+FWD_KERNEL_VERSION = "fwd-9"
 SPEC_KERNEL_VERSION = "spec-6"
 # Mixed-precision and FP64 per-point bounds against the oracle (as the GPU
 # tests state them): 64 u32 max(kappa, 1) and max(1e-12, 64 u64 kappa).

@@ -117,17 +117,24 @@ __device__ __forceinline__ Instr ld_instr(const Instr* p) {
 }
 
 // Vertex (+ propagation) of one input current x for photon polarisation pol,
-// stored as variant v of the instruction's node.
+// stored as variant v of the instruction's node.  One code path for both
+// sides, so that lanes of one round with items of both sides run the same
+// instructions: for a real 3-vector a, x (sigma.a) = (sigma.a') x with
+// a' = (ax, -ay, az), so the row vertex x eps/ is the column form with
+// eps~ = (-ex, ey, -ez) and the row propagation x (Q/ + m)/D the column form
+// with Q/D replaced by (-qx, qy, -qz); sign flips are exact.
 template <typename Real>
 __device__ __forceinline__ void vertex_store(const Instr& in, const Real x[8], int pol, int v, int nv,
                                              const Real* s_q, const Real* s_eps, Real* s_cur) {
   const Real* e3 = s_eps + (in.photon * 2 + pol) * 4;
-  const Real ev[3] = {e3[0], e3[1], e3[2]};
+  const Real sg = in.side ? (Real)-1 : (Real)1;
+  const Real ev[3] = {sg * e3[0], e3[1], sg * e3[2]};
   Real y[8], z[8];
-  if (in.side == 0) vertex_col(ev, x, y); else vertex_row(ev, x, y);
+  vertex_col(ev, x, y);
   if (in.post) {
     const Real* P = s_q + in.post * 5;
-    if (in.side == 0) prop_col(P, y, z); else prop_row(P, y, z);
+    const Real Pt[5] = {P[0], P[1], sg * P[2], P[3], sg * P[4]};
+    prop_col(Pt, y, z);
     store_cur(s_cur, in.dst, nv, v, z);
   } else {
     store_cur(s_cur, in.dst, nv, v, y);
