@@ -68,17 +68,11 @@ __device__ __forceinline__ void pauli_fma(R ax, R ay, R az, const R x[4], R y[4]
   y[3] = fma(ax, x[1], fma(ay, x[0], fma(-az, x[3], y[3])));
 }
 
-// acc += eps/ x (column) ...
+// acc += eps/ x (column form; a row node uses it with (-ex, ey, -ez))
 template <typename R>
 __device__ __forceinline__ void vacc_col(const R e[3], const R x[8], R acc[8]) {
   pauli_fma<-1>(e[0], e[1], e[2], x + 4, acc);
   pauli_fma<1>(e[0], e[1], e[2], x, acc + 4);
-}
-// ... and acc += x eps/ (row), eps/ = [[0, -s.e], [s.e, 0]]
-template <typename R>
-__device__ __forceinline__ void vacc_row(const R e[3], const R x[8], R acc[8]) {
-  pauli_fma<1>(e[0], -e[1], e[2], x + 4, acc);
-  pauli_fma<-1>(e[0], -e[1], e[2], x, acc + 4);
 }
 
 template <typename R>
@@ -193,8 +187,21 @@ __device__ __forceinline__ void vertex_sum(const KParams& p, int side, unsigned 
     vertex_input<N, SUMMED, Real>(p, side, T, j, b, v, s_spin, cur, x, pol);
     Real ev[3];
     load_e3(s_eps + (j * 2 + pol) * 4, ev);
-    if (side == 0) vacc_col(ev, x, w); else vacc_row(ev, x, w);
+    // one code path for both sides: the row form is the column form of
+    // (-ex, ey, -ez) (exact sign flips)
+    const Real sg = side ? (Real)-1 : (Real)1;
+    ev[0] *= sg;
+    ev[2] *= sg;
+    vacc_col(ev, x, w);
   }
+}
+
+// The propagator entries of a node's line in column form: a row node's
+// x (Q/ + m)/D is the column form with Q/D replaced by (-qx, qy, -qz).
+template <typename Real>
+__device__ __forceinline__ void prop_entries(const Real* P, bool row, Real Pt[5]) {
+  const Real sg = row ? (Real)-1 : (Real)1;
+  Pt[0] = P[0]; Pt[1] = P[1]; Pt[2] = sg * P[2]; Pt[3] = P[3]; Pt[4] = sg * P[4];
 }
 
 }  // namespace
@@ -272,8 +279,9 @@ qed_radj_kernel(const KParams p) {
         const unsigned post = side == 0 ? (l < H ? T : 0u) : (ALL & ~T);
         const int dst = slot_of(p, N, side, T) + v;
         if (post) {
-          Real z[8];
-          if (side == 0) prop_col(s_q + post * 5, w, z); else prop_row(s_q + post * 5, w, z);
+          Real z[8], Pt[5];
+          prop_entries(s_q + post * 5, side == 1, Pt);
+          prop_col(Pt, w, z);
           cur.st(dst, z);
         } else {
           cur.st(dst, w);
@@ -468,7 +476,12 @@ qed_radj_kernel(const KParams p) {
                 if (in_cur) cur.ld(ps_slot + vpar, wb); else adj.ld(ps_slot + vpar, wb);
                 load_e3(s_eps + (j * 2 + pl) * 4, ev);
                 // transposed vertex: column x -> eps/ x gives xbar = wbar eps/
-                if (side == 0) vacc_row(ev, wb, yb); else vacc_col(ev, wb, yb);
+                // (row form, the column form of (-ex, ey, -ez)), and the
+                // converse for a row node
+                const Real sg = side ? (Real)1 : (Real)-1;
+                ev[0] *= sg;
+                ev[2] *= sg;
+                vacc_col(ev, wb, yb);
               }
             }
           }
@@ -477,7 +490,9 @@ qed_radj_kernel(const KParams p) {
           Real wb[8];
           if (post) {
             const Real* P = s_q + post * 5;
-            if (side == 0) prop_row(P, yb, wb); else prop_col(P, yb, wb);
+            Real Pt[5];
+            prop_entries(P, side == 0, Pt);   // transposed: row form for a column node
+            prop_col(Pt, yb, wb);
             Real w[8], y[8];
             vertex_sum<N, SUMMED, Real>(p, side, T, v, s_eps, s_spin, cur, w);
             cur.ld(my + v, y);
