@@ -122,8 +122,8 @@ typedef struct {
  *     every level below the leaves; per photon set each lane of one warp
  *     builds one leaf, keeps a left leaf in registers and joins it with
  *     every right leaf of the set, from per-lane items of two ints.  A new
- *     plan starts in this form, except one fixed state in FP64 with k >= 5,
- *     where the table-driven kernel measured faster.
+ *     plan starts in this form, except one fixed state in FP64 with k other
+ *     than 3 and 4, where the table-driven kernel measured faster.
  * Both compute the same DAG; their results agree to rounding. */
 typedef enum { QED_KERNEL_TABLE = 0, QED_KERNEL_SPECIALISED = 1 } qed_kernel_form;
 

@@ -469,12 +469,15 @@ qed_status setup_fixed_join(qed_plan_s* P, bool mixed, int dev_smem, int sms) {
 }
 
 // The form a new plan starts with, from measurements on B300: the
-// specialised kernel wherever it exists, except the FP64 register-join
-// kernel of one fixed state for k >= 5 (the table kernel, bound by the FP64
-// pipe, is faster there: k = 6, 2.87 against 2.66 M points/s).
+// specialised kernel wherever it exists, except one fixed state in FP64,
+// where the table kernel (bound by the FP64 pipe; one code path for the
+// items of both sides) is faster but at k = 3 and 4: per launch, table
+// against register-join, 1.37 / 1.63 ms (k = 1, 1,048,576 points),
+// 3.65 / 4.20 (k = 2), 5.40 / 3.90 (k = 3, 524,288), 8.47 / 6.08 (k = 4,
+// 262,144), 5.15 / 7.11 (k = 5, 65,536), 5.39 / 6.12 (k = 6, 16,384).
 int default_form(const qed_plan_s* P) {
   if (!P->forms[1].ok) return 0;
-  if (!P->summed && P->prec == QED_FP64 && P->k >= 5) return 0;
+  if (!P->summed && P->prec == QED_FP64 && P->k != 3 && P->k != 4) return 0;
   return 1;
 }
 
